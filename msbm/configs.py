@@ -1,0 +1,109 @@
+"""The synthetic m-SBM workloads, by name, with their sizes and seeds.
+
+Each builder returns a dict with the graph(s) and the solve parameters.  The
+`scale` argument shrinks n (keeping degree, k, h and the split) so tests can
+run the same shape at sizes the CPU oracle finishes in seconds.
+
+Workloads (sizes as named):
+  msbm_n2000_k5_h2        n = 2,000, 5 equal clusters, 2 equal groups,
+                          p = .40 / .30 / .20 / .10, FP64 values, seed 0
+  msbm_n50k_k20_h5        n = 50,000, 20 equal clusters, 5 equal groups,
+                          mean degree 100, split 50/25/15/10, FP32, seed 1
+  msbm_n1m_k50_h10        n = 1,000,000, 50 clusters ~ Dirichlet(5),
+                          10 groups with Zipf(1) shares, mean degree 32,
+                          split 50/25/15/10, BF16 0/1 values, seed 2
+  msbm_batch256           256 graphs, n ~ logU[1e3, 6.4e4], k in {3..10},
+                          h in {2..6}, mean degree ~ U[16, 64], seed 3
+  msbm_n200k_k10_h4_gauss n = 200,000, 10 clusters, 4 groups, mean degree 48,
+                          Gaussian-kernel weights exp(-r^2 / (2 s^2)), s = 2,
+                          16-d features, seed 4
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .generator import (
+    cell_sizes_equal,
+    cell_sizes_from_proportions,
+    category_probabilities,
+    gaussian_edge_weights,
+    sample_msbm,
+)
+
+SPLIT = (0.50, 0.25, 0.15, 0.10)
+
+
+def _scaled(n: int, scale: float, minimum: int) -> int:
+    return max(minimum, int(round(n * scale)))
+
+
+def msbm_n2000_k5_h2(scale: float = 1.0):
+    n = _scaled(2000, scale, 40)
+    k, h = 5, 2
+    cells = cell_sizes_equal(n, k, h)
+    probs = {(True, True): 0.40, (True, False): 0.30, (False, True): 0.20, (False, False): 0.10}
+    g = sample_msbm(cells, probs, seed=0)
+    return {"name": "msbm_n2000_k5_h2", "graph": g, "k": k, "h": h, "value_dtype": "f64", "prec": "fp64"}
+
+
+def msbm_n50k_k20_h5(scale: float = 1.0):
+    n = _scaled(50_000, scale, 400)
+    k, h = 20, 5
+    cells = cell_sizes_equal(n, k, h)
+    probs = category_probabilities(cells, min(100.0, 0.5 * n), SPLIT)
+    g = sample_msbm(cells, probs, seed=1)
+    return {"name": "msbm_n50k_k20_h5", "graph": g, "k": k, "h": h, "value_dtype": "f32", "prec": "mixed"}
+
+
+def zipf_shares(h: int, s: float = 1.0) -> np.ndarray:
+    w = 1.0 / np.arange(1, h + 1) ** s
+    return w / w.sum()
+
+
+def msbm_n1m_k50_h10(scale: float = 1.0):
+    n = _scaled(1_000_000, scale, 2000)
+    k, h = 50, 10
+    rng = np.random.default_rng(2)
+    cluster_props = rng.dirichlet(np.full(k, 5.0))
+    cells = cell_sizes_from_proportions(n, cluster_props, zipf_shares(h))
+    probs = category_probabilities(cells, 32.0, SPLIT)
+    g = sample_msbm(cells, probs, seed=2)
+    return {"name": "msbm_n1m_k50_h10", "graph": g, "k": k, "h": h, "value_dtype": "bf16", "prec": "mixed"}
+
+
+def msbm_batch256(count: int = 256, scale: float = 1.0, seed: int = 3):
+    """Independent graphs of uneven size, with their per-graph k and h."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for t in range(count):
+        n = int(round(np.exp(rng.uniform(np.log(1000), np.log(64000))) * scale))
+        k = int(rng.integers(3, 11))
+        h = int(rng.integers(2, 7))
+        deg = float(rng.uniform(16, 64))
+        n = max(n, 4 * k * h)
+        cells = cell_sizes_equal(n, k, h)
+        probs = category_probabilities(cells, min(deg, 0.5 * n), SPLIT)
+        g = sample_msbm(cells, probs, seed=seed * 100_000 + t)
+        out.append({"graph": g, "k": k, "h": h})
+    return {"name": "msbm_batch256", "graphs": out, "value_dtype": "f32", "prec": "mixed", "block": 4}
+
+
+def msbm_n200k_k10_h4_gauss(scale: float = 1.0, bandwidth: float = 2.0):
+    n = _scaled(200_000, scale, 400)
+    k, h = 10, 4
+    cells = cell_sizes_equal(n, k, h)
+    probs = category_probabilities(cells, min(48.0, 0.5 * n), SPLIT)
+    g = sample_msbm(cells, probs, seed=4)
+    w, r2, x = gaussian_edge_weights(g, dim=16, mean_scale=2.0, bandwidth=bandwidth, seed=4)
+    g.values = w.astype(np.float32).astype(np.float64)
+    return {"name": "msbm_n200k_k10_h4_gauss", "graph": g, "k": k, "h": h, "value_dtype": "f32",
+            "prec": "mixed", "r2": r2, "features": x, "bandwidth": bandwidth}
+
+
+BUILDERS = {
+    "msbm_n2000_k5_h2": msbm_n2000_k5_h2,
+    "msbm_n50k_k20_h5": msbm_n50k_k20_h5,
+    "msbm_n1m_k50_h10": msbm_n1m_k50_h10,
+    "msbm_batch256": msbm_batch256,
+    "msbm_n200k_k10_h4_gauss": msbm_n200k_k10_h4_gauss,
+}
