@@ -1,0 +1,218 @@
+/*
+ * sfairsc.h -- C ABI of the GB300 s-FairSC library (libsfairsc.so).
+ *
+ * s-FairSC (Wang, Lu, Davidson and Bai, "Scalable Spectral Clustering with
+ * Group Fairness Constraints", AISTATS 2023, Algorithm 3) solves the fair
+ * spectral clustering problem (eq. normal-prob-fair)
+ *
+ *     min tr(H^T L H)  s.t.  H^T D H = I_k,  F^T H = 0
+ *
+ * by computing the k smallest eigenpairs of
+ *
+ *     L_n^sigma = P L_n P + sigma (I - P)                    (eq. asigma)
+ *
+ * with L_n = D^{-1/2} (D - W) D^{-1/2}, C = D^{-1/2} F, F the first h-1
+ * columns of F0 = G - 1 z^T (Lemma 2.1), P = I - C (C^T C)^{-1} C^T
+ * (eq. mv-Pw) and sigma = ||L_n||_1 (App. C), touching the operator only
+ * through w -> P(L_n(P w)) - sigma P w + sigma w (Sec. 3.4 (i)).  The
+ * embedding is H = D^{-1/2} X and the cluster labels come from k-means on
+ * the rows of H (Algorithm 3 step 4).
+ *
+ * Conventions shared by every entry point
+ *  - Pointers may be device pointers (cudaMalloc, torch CUDA tensors,
+ *    managed memory) or host pointers (pageable or pinned); the library
+ *    detects which with cudaPointerGetAttributes.  Host inputs are copied to
+ *    library-owned device buffers; host outputs are filled by a copy back.
+ *  - Integer arrays are int32, floating arrays are FP64 unless a dtype says
+ *    otherwise.  Matrices are row-major n x k unless stated.
+ *  - Every call returns an sfairsc_status (0 = success, negative = error).
+ *    No C++ exception crosses the ABI.  sfairsc_strerror() names a status.
+ *  - A context is not thread-safe; distinct contexts are independent.
+ *  - All device work is ordered on the stream given at create
+ *    (NULL = the legacy default stream).  sfairsc_solve, sfairsc_kmeans and
+ *    sfairsc_backward return after that work completes.
+ *    sfairsc_apply_operator on device buffers returns once its kernel is
+ *    enqueued.
+ */
+#ifndef SFAIRSC_H
+#define SFAIRSC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define SFAIRSC_API __attribute__((visibility("default")))
+#else
+#define SFAIRSC_API
+#endif
+
+#define SFAIRSC_ABI_VERSION 1
+#define SFAIRSC_MAX_GROUPS 32   /* h <= 32: groups are reduced with one warp lane each */
+#define SFAIRSC_MAX_BLOCK 4     /* Krylov block size b in 1..4 */
+
+typedef enum {
+  SFAIRSC_OK = 0,
+  SFAIRSC_ERR_INVALID_ARG = -1,     /* null pointer, size out of range, bad enum */
+  SFAIRSC_ERR_BAD_CSR = -2,         /* row_ptr not monotone, column out of range, self loop, negative weight */
+  SFAIRSC_ERR_ISOLATED_VERTEX = -3, /* some d_i = 0: D must be positive definite (Sec. 2.1) */
+  SFAIRSC_ERR_EMPTY_GROUP = -4,     /* some |V_s| = 0: F would lose rank h-1 (Lemma 2.1) */
+  SFAIRSC_ERR_K_TOO_LARGE = -5,     /* k > n - h + 1, the dimension of null(C^T) */
+  SFAIRSC_ERR_NONFINITE = -6,       /* NaN or Inf in the input weights */
+  SFAIRSC_ERR_NOT_CONVERGED = -7,   /* max_restarts reached; outputs hold the best Ritz pairs so far */
+  SFAIRSC_ERR_SHIFT = -8,           /* a returned eigenvalue reached sigma: sigma <= lambda_k (Prop. 3.3) */
+  SFAIRSC_ERR_CUDA = -9,            /* a CUDA runtime call failed */
+  SFAIRSC_ERR_OOM = -10,            /* device or pinned-host allocation failed */
+  SFAIRSC_ERR_DEVICE_TIMEOUT = -11, /* a bounded device-side wait gave up (the kernel returned early) */
+  SFAIRSC_ERR_UNSUPPORTED = -12,    /* a valid request outside this build's limits (h > 32, no sm_103a device) */
+  SFAIRSC_ERR_BREAKDOWN = -13       /* the Krylov block lost rank (exactly invariant subspace) */
+} sfairsc_status;
+
+typedef enum { SFAIRSC_F64 = 0, SFAIRSC_F32 = 1, SFAIRSC_BF16 = 2 } sfairsc_dtype;
+
+/* FP64: every vector, value and reduction in FP64.
+ * MIXED: Krylov vectors and SpMV in FP32 (values stored as given: FP32 or
+ * BF16); group sums, Gram-Schmidt inner products (compensated FP32 pairs),
+ * the (h-1)x(h-1) Cholesky of C^T C and the projected eigenproblem in FP64. */
+typedef enum { SFAIRSC_PREC_FP64 = 0, SFAIRSC_PREC_MIXED = 1 } sfairsc_prec;
+
+typedef struct {
+  double sigma;            /* Hotelling shift; NaN => ||L_n||_1 (App. C) */
+  double tol;              /* converged when ||A x - lambda x|| <= tol * sigma; default 1e-6 */
+  int32_t max_restarts;    /* default 200 */
+  int32_t basis;           /* Krylov basis size m; 0 => max(2k, 20) rounded to the block */
+  int32_t prec;            /* sfairsc_prec; default MIXED */
+  int32_t block;           /* Krylov block size 1..4; default 1 */
+  uint64_t seed;           /* start block of the eigensolver; default 1 */
+  uint64_t kmeans_seed;    /* splitmix64 seed of k-means++; default 0 */
+  int32_t kmeans_n_init;   /* replicates, best inertia wins; default 1 */
+  int32_t kmeans_max_iter; /* Lloyd assignments per replicate; default 100 */
+  int32_t validate;        /* 0: none, 1: structure checks (default), 2: also symmetry (sorted columns) */
+  int32_t reserved[9];
+} sfairsc_opts;
+
+typedef struct {
+  int32_t status;          /* same value the call returned */
+  int32_t restarts;        /* thick restarts performed */
+  int32_t matvecs;         /* operator applications (counting each of the b block columns) */
+  int32_t kmeans_iters;    /* Lloyd assignments of the winning replicate */
+  double sigma;            /* shift used */
+  double max_resid;        /* max_i ||A x_i - lambda_i x_i||_2 / sigma, FP64 operator, ||x_i|| = 1 */
+  double fairness_err;     /* max |F^T H| over entries */
+  double dorth_err;        /* max |H^T D H - I| over entries */
+  double kmeans_inertia;   /* sum of squared distances of the winning replicate */
+  float ms_setup, ms_solve, ms_kmeans, ms_total;
+  int32_t reserved[8];
+} sfairsc_info;
+
+typedef struct sfairsc_ctx sfairsc_ctx;
+
+/* Human-readable name of a status code; never NULL. */
+SFAIRSC_API const char* sfairsc_strerror(int status);
+
+/* Detail message of the last failing call on this thread ("" after a
+ * success); valid until the next call on this thread.  Never NULL. */
+SFAIRSC_API const char* sfairsc_last_error(void);
+
+/* Fill *opts with the defaults listed above.  Errors: INVALID_ARG if opts is NULL. */
+SFAIRSC_API int sfairsc_opts_default(sfairsc_opts* opts);
+
+/*
+ * Build a solver context for one graph (Algorithm 3 steps 1-2).
+ *
+ * n, nnz        vertices and stored entries (both triangles of the symmetric W)
+ * row_ptr       int32[n+1], row_ptr[0] = 0, nondecreasing, row_ptr[n] = nnz
+ * col_idx       int32[nnz], column of each entry, in [0, n), no diagonal
+ * values        nnz weights w_ij >= 0 of dtype value_dtype (sfairsc_dtype);
+ *               W must be symmetric (checked only with validate = 2)
+ * group_labels  int32[n], group of each vertex in [0, h) (eq. group-vec);
+ *               F is built from them per Lemma 2.1 and never stored
+ * h             number of groups, 1..32 (h = 1: plain SC, Algorithm 1)
+ * k             number of eigenpairs and clusters, 1 <= k <= n - h + 1
+ * normalized    1: the paper's normalized problem.  0: an extension the
+ *               paper does not define: L = D - W, P = I - F (F^T F)^{-1} F^T,
+ *               sigma = ||L||_1, H = X.
+ * opts          NULL for defaults
+ * cuda_stream   cudaStream_t to order all work on (NULL = default stream)
+ *
+ * Ownership: device inputs are borrowed and must stay valid and unchanged
+ * until sfairsc_destroy; host inputs are copied.  The context owns its
+ * workspace (Krylov basis, projected matrix, scratch), allocated here.
+ * Computes the degrees d_i = sum_j w_ij (Sec. 2.1), d^{-1/2}, the group
+ * sizes and sums S_s = sum_{i in V_s} 1/d_i, C^T C in closed form from them,
+ * its Cholesky factor, and sigma.
+ * Errors: INVALID_ARG, BAD_CSR, ISOLATED_VERTEX, EMPTY_GROUP, K_TOO_LARGE,
+ * NONFINITE, UNSUPPORTED, CUDA, OOM.  On error *out is NULL.
+ */
+SFAIRSC_API int sfairsc_create(sfairsc_ctx** out, int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
+                   const void* values, int32_t value_dtype, const int32_t* group_labels, int32_t h, int32_t k,
+                   int32_t normalized, const sfairsc_opts* opts, void* cuda_stream);
+
+/* Release the context and its workspace.  NULL is accepted.  Returns OK or CUDA. */
+SFAIRSC_API int sfairsc_destroy(sfairsc_ctx* ctx);
+
+/* The shift sigma in use (Sec. 3.4 (iii), App. C).  Errors: INVALID_ARG. */
+SFAIRSC_API int sfairsc_get_sigma(const sfairsc_ctx* ctx, double* sigma);
+
+/*
+ * out = L_n^sigma w for nvec vectors at once (Sec. 3.4 (i)-(ii)):
+ * P(L_n(P w)) - sigma P w + sigma w, in one fused kernel.
+ * w, out: n x nvec COLUMN-major (each vector contiguous), FP64 when the
+ * context precision is FP64 and FP32 when it is MIXED; nvec in 1..4.
+ * w and out must not overlap.  Errors: INVALID_ARG, CUDA, DEVICE_TIMEOUT.
+ */
+SFAIRSC_API int sfairsc_apply_operator(sfairsc_ctx* ctx, const void* w, void* out, int32_t nvec);
+
+/*
+ * Algorithm 3 steps 3-4: the k smallest eigenpairs of L_n^sigma by a
+ * thick-restart block Lanczos with CGS2 reorthogonalisation, then
+ * H = D^{-1/2} X and seeded k-means on the rows of H.
+ * eigenvalues  double[k], ascending (FP64 Rayleigh quotients of the final vectors)
+ * H            double[n*k] row-major, H^T D H = I; each column's largest-magnitude
+ *              entry (lowest row on ties) is positive.  May be NULL.
+ * labels       int32[n] cluster of each vertex in [0, k).  May be NULL (no k-means).
+ * info         may be NULL.
+ * Errors: INVALID_ARG, NOT_CONVERGED (outputs still written), SHIFT, CUDA,
+ * DEVICE_TIMEOUT, BREAKDOWN.
+ */
+SFAIRSC_API int sfairsc_solve(sfairsc_ctx* ctx, double* eigenvalues, double* H, int32_t* labels, sfairsc_info* info);
+
+/*
+ * Seeded k-means on the rows of an n x d FP64 row-major matrix (Algorithm 3
+ * step 4), exactly reproducible: float32 distances in dimension order,
+ * splitmix64 counter draws, k-means++ with integer-quantised D^2 weights,
+ * Lloyd with fixed-point exact centroid sums (the full rule set is stated
+ * in the library's k-means source).
+ * labels int32[n]; centroids double[kc*d] (may be NULL); inertia double[1] (may be NULL).
+ * Errors: INVALID_ARG, CUDA, OOM.
+ */
+SFAIRSC_API int sfairsc_kmeans(int64_t n, int32_t d, const double* X, int32_t kc, uint64_t seed, int32_t n_init,
+                   int32_t max_iter, int32_t* labels, double* centroids, double* inertia, int32_t* iterations,
+                   void* cuda_stream);
+
+/*
+ * Gradient of f = sum_i gbar_i lambda_i with respect to the stored weights,
+ * after a successful sfairsc_solve on this context:
+ *   d lambda_i / d w_ab = (h_ai - h_bi)^2 - lambda_i (h_ai^2 + h_bi^2)
+ * for the undirected weight w_ab = w_ba (first-order perturbation of the
+ * pencil (Z^T L Z, Z^T D Z) of Algorithm 2, whose Z does not depend on W);
+ * each CSR entry receives half, so summing over both entries gives the
+ * undirected derivative.  One pass over W's sparsity pattern (SDDMM).
+ * grad_lambda   double[k] (gbar)
+ * grad_values   double[nnz] output
+ * bandwidth     s > 0 when the weights are w = exp(-r^2/(2 s^2)); then
+ *               *grad_bandwidth = sum_e g_e w_e (-2 ln w_e) / s.  Pass
+ *               bandwidth <= 0 or grad_bandwidth = NULL to skip it.
+ * Errors: INVALID_ARG (no solve yet), CUDA.
+ */
+SFAIRSC_API int sfairsc_backward(sfairsc_ctx* ctx, const double* grad_lambda, double* grad_values, double bandwidth,
+                     double* grad_bandwidth);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SFAIRSC_H */

@@ -1,0 +1,170 @@
+"""ctypes binding of libsfairsc.so: the C entry points under the same names.
+
+This module only marshals arguments (pointers, sizes, enums); every step of
+the computation runs inside the CUDA library.  Importing it does not load the
+library; the first call does, and raises if the library is missing — there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+from . import buildlib as _build
+
+SFAIRSC_F64, SFAIRSC_F32, SFAIRSC_BF16 = 0, 1, 2
+SFAIRSC_PREC_FP64, SFAIRSC_PREC_MIXED = 0, 1
+STATUS = {
+    0: "OK", -1: "INVALID_ARG", -2: "BAD_CSR", -3: "ISOLATED_VERTEX", -4: "EMPTY_GROUP", -5: "K_TOO_LARGE",
+    -6: "NONFINITE", -7: "NOT_CONVERGED", -8: "SHIFT", -9: "CUDA", -10: "OOM", -11: "DEVICE_TIMEOUT",
+    -12: "UNSUPPORTED", -13: "BREAKDOWN",
+}
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [
+        ("sigma", ctypes.c_double), ("tol", ctypes.c_double), ("max_restarts", ctypes.c_int32),
+        ("basis", ctypes.c_int32), ("prec", ctypes.c_int32), ("block", ctypes.c_int32),
+        ("seed", ctypes.c_uint64), ("kmeans_seed", ctypes.c_uint64), ("kmeans_n_init", ctypes.c_int32),
+        ("kmeans_max_iter", ctypes.c_int32), ("validate", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9),
+    ]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int32), ("restarts", ctypes.c_int32), ("matvecs", ctypes.c_int32),
+        ("kmeans_iters", ctypes.c_int32), ("sigma", ctypes.c_double), ("max_resid", ctypes.c_double),
+        ("fairness_err", ctypes.c_double), ("dorth_err", ctypes.c_double), ("kmeans_inertia", ctypes.c_double),
+        ("ms_setup", ctypes.c_float), ("ms_solve", ctypes.c_float), ("ms_kmeans", ctypes.c_float),
+        ("ms_total", ctypes.c_float), ("reserved", ctypes.c_int32 * 8),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class SFairSCError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({status}) {detail}".rstrip())
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.library_path()
+
+
+def load(path: str | None = None):
+    """Load libsfairsc.so once.  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or library_path()
+    if not os.path.exists(p):
+        raise RuntimeError(f"libsfairsc.so not built at {p}; run paper_2210_16435_gb300.buildlib.build() "
+                           "(the CUDA library is required: there is no CPU fallback)")
+    lib = ctypes.CDLL(p)
+    vp, i32, i64, u64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+    lib.sfairsc_strerror.restype = ctypes.c_char_p
+    lib.sfairsc_strerror.argtypes = [ctypes.c_int]
+    lib.sfairsc_last_error.restype = ctypes.c_char_p
+    lib.sfairsc_last_error.argtypes = []
+    lib.sfairsc_opts_default.argtypes = [ctypes.POINTER(Opts)]
+    lib.sfairsc_create.argtypes = [ctypes.POINTER(vp), i64, i64, vp, vp, vp, i32, vp, i32, i32, i32,
+                                   ctypes.POINTER(Opts), vp]
+    lib.sfairsc_destroy.argtypes = [vp]
+    lib.sfairsc_get_sigma.argtypes = [vp, ctypes.POINTER(dbl)]
+    lib.sfairsc_apply_operator.argtypes = [vp, vp, vp, i32]
+    lib.sfairsc_solve.argtypes = [vp, vp, vp, vp, ctypes.POINTER(Info)]
+    lib.sfairsc_kmeans.argtypes = [i64, i32, vp, i32, u64, i32, i32, vp, vp, vp, vp, vp]
+    lib.sfairsc_backward.argtypes = [vp, vp, vp, dbl, vp]
+    for f in ("sfairsc_opts_default", "sfairsc_create", "sfairsc_destroy", "sfairsc_get_sigma",
+              "sfairsc_apply_operator", "sfairsc_solve", "sfairsc_kmeans", "sfairsc_backward"):
+        getattr(lib, f).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, where: str, ok=(0,)):
+    if rc not in ok:
+        raise SFairSCError(rc, where, load().sfairsc_last_error().decode())
+    return rc
+
+
+def sfairsc_strerror(status: int) -> str:
+    return load().sfairsc_strerror(status).decode()
+
+
+def sfairsc_opts_default() -> Opts:
+    o = Opts()
+    _check(load().sfairsc_opts_default(ctypes.byref(o)), "sfairsc_opts_default")
+    return o
+
+
+def sfairsc_create(n, nnz, row_ptr, col_idx, values, value_dtype, group_labels, h, k, normalized=1, opts=None,
+                   stream=None) -> int:
+    """Returns the context handle (int).  Pointer arguments are integer addresses."""
+    ctx = ctypes.c_void_p()
+    rc = load().sfairsc_create(ctypes.byref(ctx), int(n), int(nnz), row_ptr, col_idx, values, int(value_dtype),
+                               group_labels, int(h), int(k), int(normalized),
+                               ctypes.byref(opts) if opts is not None else None, stream)
+    _check(rc, "sfairsc_create")
+    return ctx.value
+
+
+def sfairsc_destroy(ctx) -> None:
+    _check(load().sfairsc_destroy(ctx), "sfairsc_destroy")
+
+
+def sfairsc_get_sigma(ctx) -> float:
+    s = ctypes.c_double()
+    _check(load().sfairsc_get_sigma(ctx, ctypes.byref(s)), "sfairsc_get_sigma")
+    return s.value
+
+
+def sfairsc_apply_operator(ctx, w, out, nvec: int) -> None:
+    _check(load().sfairsc_apply_operator(ctx, w, out, int(nvec)), "sfairsc_apply_operator")
+
+
+def sfairsc_solve(ctx, eigenvalues, H, labels, allow=(0,)) -> tuple[int, Info]:
+    info = Info()
+    rc = load().sfairsc_solve(ctx, eigenvalues, H, labels, ctypes.byref(info))
+    _check(rc, "sfairsc_solve", ok=allow)
+    return rc, info
+
+
+def sfairsc_kmeans(n, d, X, kc, seed, n_init, max_iter, labels, centroids=None, stream=None):
+    inertia = ctypes.c_double()
+    iters = ctypes.c_int32()
+    rc = load().sfairsc_kmeans(int(n), int(d), X, int(kc), int(seed), int(n_init), int(max_iter), labels, centroids,
+                               ctypes.byref(inertia), ctypes.byref(iters), stream)
+    _check(rc, "sfairsc_kmeans")
+    return inertia.value, iters.value
+
+
+def sfairsc_backward(ctx, grad_lambda, grad_values, bandwidth=0.0, want_bandwidth=False):
+    gs = ctypes.c_double()
+    rc = load().sfairsc_backward(ctx, grad_lambda, grad_values, float(bandwidth),
+                                 ctypes.byref(gs) if want_bandwidth else None)
+    _check(rc, "sfairsc_backward")
+    return gs.value if want_bandwidth else None
+
+
+def make_opts(prec="mixed", block=1, tol=1e-6, basis=0, max_restarts=200, sigma=None, seed=1, kmeans_seed=0,
+              kmeans_n_init=1, kmeans_max_iter=100, validate=1) -> Opts:
+    o = sfairsc_opts_default()
+    o.prec = SFAIRSC_PREC_FP64 if prec == "fp64" else SFAIRSC_PREC_MIXED
+    o.block = int(block)
+    o.tol = float(tol)
+    o.basis = int(basis)
+    o.max_restarts = int(max_restarts)
+    o.sigma = math.nan if sigma is None else float(sigma)
+    o.seed = int(seed)
+    o.kmeans_seed = int(kmeans_seed)
+    o.kmeans_n_init = int(kmeans_n_init)
+    o.kmeans_max_iter = int(kmeans_max_iter)
+    o.validate = int(validate)
+    return o

@@ -1,0 +1,841 @@
+// C entry points of libsfairsc.so (declared in include/sfairsc.h).
+//
+// sfairsc_create: validation and the setup pass of Algorithm 3 steps 1-2.
+// sfairsc_solve:  Algorithm 3 steps 3-4 -- a thick-restart block Lanczos on
+//   L_n^sigma (eq. asigma), touching the operator only through the fused
+//   kernel of Sec. 3.4 (i)-(ii); FP64 Rayleigh quotients and residuals of the
+//   final vectors; H = D^{-1/2} X; seeded k-means on the rows of H.
+// The thick restart keeps the K best Ritz vectors plus the next block, which
+// is mathematically the implicit restart of ARPACK with exact shifts that the
+// paper's eigs performs (Sec. 3.4 (i)).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace sfairsc {
+
+struct SfError {
+  int code;
+  std::string msg;
+};
+
+static thread_local std::string g_last_error;
+
+void check_cuda(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    if (e == cudaErrorMemoryAllocation) throw SfError{SFAIRSC_ERR_OOM, std::string(what) + ": out of memory"};
+    throw SfError{SFAIRSC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e)};
+  }
+}
+
+void fail(int code, const std::string& msg) { throw SfError{code, msg}; }
+
+static bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  const cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static size_t dtype_size(int dt) { return dt == SFAIRSC_F64 ? 8 : dt == SFAIRSC_F32 ? 4 : 2; }
+
+}  // namespace sfairsc
+
+using namespace sfairsc;
+
+struct sfairsc_ctx {
+  int64_t n = 0, nnz = 0;
+  int h = 1, k = 1, normalized = 1;
+  int vdt = SFAIRSC_F64;  // dtype of the stored values the operator reads
+  int vdt_orig = SFAIRSC_F64;
+  sfairsc_opts opts{};
+  cudaStream_t stream = nullptr;
+  VecType vt = VecType::F32;
+  int B = 1, m = 20;
+  int64_t ldv = 0;
+  int ldh = 0;
+  int sms = 0;
+  double sigma = 0.0;
+  std::vector<double> z;
+
+  const int32_t* row_ptr = nullptr;
+  const int32_t* col = nullptr;
+  const void* val = nullptr;       // values read by the main operator
+  const void* val_orig = nullptr;  // values as given (FP64 final check)
+  std::vector<void*> owned;
+
+  uint8_t* lab = nullptr;
+  double* deg = nullptr;
+  double* dinv64 = nullptr;
+  float* dinv32 = nullptr;
+  double* params = nullptr;
+  double* params_host = nullptr;
+
+  // operator workspace
+  OpPlan op;      // main precision
+  OpPlan op64;    // FP64 vectors, original values (final residual check)
+  void* ytil = nullptr;
+  double* ytil64 = nullptr;
+  double* op_partial = nullptr;
+  int32_t* cta_rows = nullptr;
+  int32_t* cta_rows_orth = nullptr;
+  unsigned* barrier = nullptr;
+  unsigned* err = nullptr;
+
+  // Krylov workspace
+  void* V = nullptr;
+  void* U = nullptr;
+  double* Hd = nullptr;
+  double* Yd = nullptr;
+  double* orth_partial = nullptr;
+  double* orth_coef = nullptr;
+  OrthPlan orth;
+  double* Hh = nullptr;  // pinned host copy of the projected matrix
+  double* Yh = nullptr;  // pinned host
+
+  // results for backward / outputs
+  double* X64 = nullptr;  // n x k column-major
+  double* AX64 = nullptr;
+  double* Hres = nullptr;  // n x k row-major
+  double* lam_d = nullptr;
+  double* stat_partial = nullptr;
+  int stat_blocks = 0;
+  unsigned long long* colkey = nullptr;
+  double* diag_partial = nullptr;
+  int diag_blocks = 0;
+  double* bw_partial = nullptr;
+  double* bw_A = nullptr;
+  int bw_blocks = 0;
+  int32_t* labels_d = nullptr;
+  std::vector<double> lam_h;
+  bool solved = false;
+
+  template <typename T>
+  T* dalloc(size_t count) {
+    void* p = nullptr;
+    check_cuda(cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T)), "device allocation");
+    owned.push_back(p);
+    return static_cast<T*>(p);
+  }
+  ~sfairsc_ctx() {
+    for (void* p : owned) cudaFree(p);
+    if (Hh) cudaFreeHost(Hh);
+    if (Yh) cudaFreeHost(Yh);
+    if (params_host) cudaFreeHost(params_host);
+  }
+};
+
+namespace {
+
+template <typename F>
+int guarded(F&& f) {
+  try {
+    f();
+    g_last_error.clear();
+    return SFAIRSC_OK;
+  } catch (const SfError& e) {
+    g_last_error = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return SFAIRSC_ERR_OOM;
+  } catch (...) {
+    g_last_error = "unexpected internal error";
+    return SFAIRSC_ERR_CUDA;
+  }
+}
+
+// Copy a host array to a new owned device buffer, or borrow a device pointer.
+template <typename T>
+const T* to_device(sfairsc_ctx* c, const T* p, size_t count, size_t elem = sizeof(T)) {
+  if (is_device_ptr(p)) return p;
+  void* d = nullptr;
+  check_cuda(cudaMalloc(&d, std::max<size_t>(count * elem, 1)), "device allocation");
+  c->owned.push_back(d);
+  check_cuda(cudaMemcpyAsync(d, p, count * elem, cudaMemcpyHostToDevice, c->stream), "host to device copy");
+  return static_cast<const T*>(d);
+}
+
+__global__ void f64_to_f32_kernel(int64_t n, const double* in, float* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
+int next_pow2(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_idx, const void* values,
+                   const int32_t* labels) {
+  cudaStream_t s = c->stream;
+  const int n = (int)c->n;
+  int dev = 0;
+  check_cuda(cudaGetDevice(&dev), "get device");
+  cudaDeviceProp prop;
+  check_cuda(cudaGetDeviceProperties(&prop, dev), "device properties");
+  if (prop.major < 10) fail(SFAIRSC_ERR_UNSUPPORTED, "needs a Blackwell (sm_10x) GPU");
+  c->sms = prop.multiProcessorCount;
+
+  c->row_ptr = to_device(c, row_ptr, (size_t)n + 1);
+  c->col = to_device(c, col_idx, (size_t)c->nnz);
+  c->val_orig = to_device(c, static_cast<const unsigned char*>(values), (size_t)c->nnz, dtype_size(c->vdt_orig));
+  const int32_t* lab_in = to_device(c, labels, (size_t)n);
+
+  unsigned* flags = c->dalloc<unsigned>(4);
+  check_cuda(cudaMemsetAsync(flags, 0, 4 * sizeof(unsigned), s), "memset");
+  if (c->opts.validate > 0)
+    launch_validate(n, c->nnz, c->row_ptr, c->col, c->val_orig, c->vdt_orig, lab_in, c->h, c->opts.validate >= 2,
+                    flags, s);
+  unsigned hf = 0;
+  check_cuda(cudaMemcpyAsync(&hf, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "d2h");
+  check_cuda(cudaStreamSynchronize(s), "validate");
+  if (hf & ((1u << 0) | (1u << 1) | (1u << 2) | (1u << 6) | (1u << 7)))
+    fail(SFAIRSC_ERR_BAD_CSR, "CSR structure invalid (row_ptr, column range, self loop or symmetry)");
+  if (hf & (1u << 4)) fail(SFAIRSC_ERR_NONFINITE, "non-finite edge weight");
+  if (hf & (1u << 3)) fail(SFAIRSC_ERR_BAD_CSR, "negative edge weight");
+  if (hf & (1u << 5)) fail(SFAIRSC_ERR_INVALID_ARG, "group label outside [0, h)");
+
+  // degrees, D^{-1/2}, group sums
+  c->lab = c->dalloc<uint8_t>(n);
+  c->deg = c->dalloc<double>(n);
+  c->dinv64 = c->dalloc<double>(n);
+  c->dinv32 = c->dalloc<float>(n);
+  const int nb = degrees_blocks(n);
+  double* bsum = c->dalloc<double>((size_t)nb * 2 * c->h);
+  check_cuda(cudaMemsetAsync(flags, 0, sizeof(unsigned), s), "memset");
+  launch_degrees(n, c->row_ptr, c->val_orig, c->vdt_orig, lab_in, c->lab, c->deg, c->dinv64, c->dinv32, bsum, nb, c->h,
+                 c->normalized, flags, s);
+  std::vector<double> hb((size_t)nb * 2 * c->h);
+  check_cuda(cudaMemcpyAsync(hb.data(), bsum, hb.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "d2h");
+  check_cuda(cudaMemcpyAsync(&hf, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "d2h");
+  check_cuda(cudaStreamSynchronize(s), "degrees");
+  if (hf & (1u << 8)) fail(SFAIRSC_ERR_ISOLATED_VERTEX, "a vertex has zero degree (D must be positive definite)");
+  const int h = c->h;
+  std::vector<double> cnt(h, 0.0), S(h, 0.0);
+  for (int b = 0; b < nb; ++b)
+    for (int g = 0; g < h; ++g) {
+      cnt[g] += hb[((size_t)b * h + g) * 2 + 0];
+      S[g] += hb[((size_t)b * h + g) * 2 + 1];
+    }
+  for (int g = 0; g < h; ++g)
+    if (cnt[g] < 0.5) fail(SFAIRSC_ERR_EMPTY_GROUP, "group " + std::to_string(g) + " is empty");
+  if (c->k > n - h + 1) fail(SFAIRSC_ERR_K_TOO_LARGE, "k exceeds n - h + 1");
+
+  // C^T C in closed form and its Cholesky factor (Lemma 2.1: SPD)
+  c->z.assign(h, 0.0);
+  double Ssum = 0.0;
+  for (int g = 0; g < h; ++g) {
+    c->z[g] = cnt[g] / (double)n;
+    Ssum += S[g];
+  }
+  check_cuda(cudaMallocHost((void**)&c->params_host, sizeof(double) * kParams), "pinned allocation");
+  double* P = c->params_host;
+  std::fill(P, P + kParams, 0.0);
+  for (int g = 0; g < h; ++g) P[kPZ + g] = c->z[g];
+  const int p = h - 1;
+  std::vector<double> M((size_t)std::max(p, 1) * std::max(p, 1), 0.0);
+  for (int a = 0; a < p; ++a)
+    for (int b = 0; b < p; ++b)
+      M[(size_t)a * p + b] = (a == b ? S[a] : 0.0) - c->z[b] * S[a] - c->z[a] * S[b] + c->z[a] * c->z[b] * Ssum;
+  for (int a = 0; a < p; ++a) {
+    for (int b = 0; b <= a; ++b) {
+      double sum = M[(size_t)a * p + b];
+      for (int q = 0; q < b; ++q) sum -= P[kPL + a * kLStride + q] * P[kPL + b * kLStride + q];
+      if (a == b) {
+        if (!(sum > 0.0)) fail(SFAIRSC_ERR_EMPTY_GROUP, "C^T C is not positive definite");
+        P[kPL + a * kLStride + a] = std::sqrt(sum);
+      } else {
+        P[kPL + a * kLStride + b] = sum / P[kPL + b * kLStride + b];
+      }
+    }
+  }
+  // sigma = ||L_n||_1 unless given
+  if (std::isnan(c->opts.sigma)) {
+    double* bmax = c->dalloc<double>((n + 255) / 256);
+    launch_sigma_rows(n, c->row_ptr, c->col, c->val_orig, c->vdt_orig, c->dinv64, c->deg, c->normalized, bmax,
+                      (n + 255) / 256, s);
+    std::vector<double> hm((n + 255) / 256);
+    check_cuda(cudaMemcpyAsync(hm.data(), bmax, hm.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "d2h");
+    check_cuda(cudaStreamSynchronize(s), "sigma");
+    c->sigma = *std::max_element(hm.begin(), hm.end());
+  } else {
+    c->sigma = c->opts.sigma;
+  }
+  P[kPSigma] = c->sigma;
+  c->params = c->dalloc<double>(kParams);
+  check_cuda(cudaMemcpyAsync(c->params, P, sizeof(double) * kParams, cudaMemcpyHostToDevice, s), "h2d");
+
+  // values read by the operator: FP32 copy of FP64 values in the mixed path
+  c->val = c->val_orig;
+  c->vdt = c->vdt_orig;
+  if (c->vt == VecType::F32 && c->vdt_orig == SFAIRSC_F64) {
+    float* v32 = c->dalloc<float>((size_t)c->nnz);
+    f64_to_f32_kernel<<<1024, 256, 0, s>>>(c->nnz, (const double*)c->val_orig, v32);
+    check_cuda(cudaGetLastError(), "value conversion");
+    c->val = v32;
+    c->vdt = SFAIRSC_F32;
+  }
+
+  // operator plans
+  const int threads = 1024;
+  const size_t smem_f = operator_smem_bytes(threads, h, 4, c->vt);
+  const size_t smem_d = operator_smem_bytes(threads, h, 4, VecType::F64);
+  const int gmax = std::min(operator_max_grid(c->vt, c->vdt, 4, threads, smem_f),
+                            operator_max_grid(VecType::F64, c->vdt_orig, 4, threads, smem_d));
+  if (gmax < 1) fail(SFAIRSC_ERR_UNSUPPORTED, "operator kernel does not fit on this device");
+  const long long work = c->nnz + 16ll * n;
+  const int grid = (int)std::max(1ll, std::min<long long>(gmax, (work + 16383) / 16384));
+  c->cta_rows = c->dalloc<int32_t>(grid + 1);
+  launch_row_partition(n, c->row_ptr, grid, 16, c->cta_rows, s);
+  const double avg = (double)c->nnz / std::max(n, 1);
+  const int lanes = std::min(32, std::max(4, next_pow2((int)std::ceil(avg / 4.0))));
+  const size_t vs = c->vt == VecType::F64 ? 8 : 4;
+  c->ytil = c->dalloc<unsigned char>((size_t)n * 4 * vs);
+  c->ytil64 = c->dalloc<double>((size_t)n * 4);
+  c->op_partial = c->dalloc<double>((size_t)grid * kMaxGroups * 4);
+  c->barrier = c->dalloc<unsigned>(4);
+  c->err = c->barrier + 2;
+  check_cuda(cudaMemsetAsync(c->barrier, 0, 4 * sizeof(unsigned), s), "memset");
+  OpPlan& o = c->op;
+  o.n = n;
+  o.h = h;
+  o.normalized = c->normalized;
+  o.grid = grid;
+  o.threads = threads;
+  o.lanes_per_row = lanes;
+  o.row_ptr = c->row_ptr;
+  o.col = c->col;
+  o.val = c->val;
+  o.val_dtype = c->vdt;
+  o.lab = c->lab;
+  o.dinv = c->vt == VecType::F64 ? (const void*)c->dinv64 : (const void*)c->dinv32;
+  o.deg = c->deg;
+  o.params = c->params;
+  o.ytil = c->ytil;
+  o.partial = c->op_partial;
+  o.cta_rows = c->cta_rows;
+  o.barrier = c->barrier;
+  o.err = c->err;
+  c->op64 = o;
+  c->op64.val = c->val_orig;
+  c->op64.val_dtype = c->vdt_orig;
+  c->op64.dinv = c->dinv64;
+  c->op64.ytil = c->ytil64;
+
+  // Krylov basis
+  c->B = std::max(1, std::min(SFAIRSC_MAX_BLOCK, c->opts.block));
+  if (c->B == 3) c->B = 4;
+  int m = c->opts.basis > 0 ? c->opts.basis : std::max(2 * c->k, 20);
+  m = std::max(m, c->k + c->B);
+  m = (m + c->B - 1) / c->B * c->B;
+  const int mcap = (n / c->B) * c->B - c->B;
+  if (m > mcap) m = mcap;
+  if (m < c->k + c->B || m + c->B > 256) {
+    if (m + c->B > 256) fail(SFAIRSC_ERR_UNSUPPORTED, "Krylov basis larger than 252 columns");
+    fail(SFAIRSC_ERR_K_TOO_LARGE, "graph too small for k and the block size");
+  }
+  c->m = m;
+  c->ldv = (m + c->B + 3) / 4 * 4;
+  c->ldh = m + c->B;
+  c->V = c->dalloc<unsigned char>((size_t)n * c->ldv * vs);
+  c->U = c->dalloc<unsigned char>((size_t)n * 4 * vs);
+  check_cuda(cudaMemsetAsync(c->U, 0, (size_t)n * 4 * vs, s), "memset");
+  c->Hd = c->dalloc<double>((size_t)c->ldh * m);
+  c->Yd = c->dalloc<double>((size_t)m * m);
+  const int ogmax = orth_max_grid(c->vt, c->B, 512);
+  const int ogrid = std::max(1, std::min(ogmax, (n + 511) / 512));
+  const int stride = 8 * 32 * 4 + 16;
+  c->orth_partial = c->dalloc<double>((size_t)ogrid * stride);
+  c->orth_coef = c->dalloc<double>(8 * 32 * 4);
+  c->cta_rows_orth = c->dalloc<int32_t>(ogrid + 1);
+  std::vector<int32_t> orows(ogrid + 1);
+  for (int t = 0; t <= ogrid; ++t) orows[t] = (int32_t)((long long)t * n / ogrid);
+  check_cuda(cudaMemcpyAsync(c->cta_rows_orth, orows.data(), sizeof(int32_t) * (ogrid + 1), cudaMemcpyHostToDevice, s),
+             "h2d");
+  OrthPlan& q = c->orth;
+  q.n = n;
+  q.grid = ogrid;
+  q.threads = 512;
+  q.ldv = c->ldv;
+  q.V = c->V;
+  q.U = c->U;
+  q.H = c->Hd;
+  q.ldh = c->ldh;
+  q.partial = c->orth_partial;
+  q.coef = c->orth_coef;
+  q.cta_rows = c->cta_rows_orth;
+  q.barrier = c->barrier;
+  q.err = c->err;
+  check_cuda(cudaMallocHost((void**)&c->Hh, sizeof(double) * c->ldh * m), "pinned allocation");
+  check_cuda(cudaMallocHost((void**)&c->Yh, sizeof(double) * m * m), "pinned allocation");
+
+  // final-stage buffers
+  const int k = c->k;
+  c->X64 = c->dalloc<double>((size_t)n * k);
+  c->AX64 = c->dalloc<double>((size_t)n * k);
+  c->Hres = c->dalloc<double>((size_t)n * k);
+  c->lam_d = c->dalloc<double>(k);
+  c->stat_blocks = std::max(1, std::min(2 * c->sms, (n + 1023) / 1024));
+  c->stat_partial = c->dalloc<double>((size_t)c->stat_blocks * k * 3);
+  c->colkey = c->dalloc<unsigned long long>(2 * (size_t)k);
+  c->diag_blocks = std::max(1, std::min(2 * c->sms, (n + 1023) / 1024));
+  c->diag_partial = c->dalloc<double>((size_t)c->diag_blocks * ((size_t)h * k + (size_t)k * k));
+  c->bw_blocks = std::max(1, std::min(4 * c->sms, (n + 7) / 8));
+  c->bw_partial = c->dalloc<double>(c->bw_blocks);
+  c->bw_A = c->dalloc<double>(n);
+  c->labels_d = c->dalloc<int32_t>(n);
+  check_cuda(cudaStreamSynchronize(s), "create");
+}
+
+void check_err_word(sfairsc_ctx* c) {
+  unsigned e = 0;
+  check_cuda(cudaMemcpyAsync(&e, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream), "d2h");
+  check_cuda(cudaStreamSynchronize(c->stream), "sync");
+  if (e) {
+    check_cuda(cudaMemsetAsync(c->barrier, 0, 4 * sizeof(unsigned), c->stream), "memset");
+    check_cuda(cudaStreamSynchronize(c->stream), "sync");
+    if (e & kErrBarrierTimeout) fail(SFAIRSC_ERR_DEVICE_TIMEOUT, "a grid barrier timed out");
+    if (e & kErrBreakdown) fail(SFAIRSC_ERR_BREAKDOWN, "Krylov block lost rank");
+  }
+}
+
+void apply_op(sfairsc_ctx* c, bool fp64, const void* w, int64_t wrs, int64_t wcs, void* out, int64_t ors, int64_t ocs,
+              int nvec) {
+  const OpPlan& p = fp64 ? c->op64 : c->op;
+  launch_operator(p, fp64 ? VecType::F64 : c->vt, w, wrs, wcs, out, ors, ocs, nvec, c->stream);
+}
+
+struct Timer {
+  cudaEvent_t a, b;
+  explicit Timer(cudaStream_t s) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, s);
+  }
+  float stop(cudaStream_t s) {
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return ms;
+  }
+};
+
+int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* labels, sfairsc_info* info) {
+  cudaStream_t s = c->stream;
+  const int n = (int)c->n, k = c->k, B = c->B, m = c->m, ldh = c->ldh;
+  const size_t vs = c->vt == VecType::F64 ? 8 : 4;
+  sfairsc_info inf{};
+  inf.sigma = c->sigma;
+  Timer tsolve(s);
+  // start block -> U, orthonormalise into V[:, 0:B]
+  launch_random_block(c->vt, n, c->U, 4, B, c->opts.seed, s);
+  launch_orth(c->orth, c->vt, 0, -1, B, s);
+  check_cuda(cudaMemsetAsync(c->Hd, 0, sizeof(double) * ldh * m, s), "memset");
+  int j0 = 0;
+  int restarts = 0, matvecs = 0;
+  std::vector<double> T((size_t)m * m), theta(m), resid(m);
+  bool converged = false;
+  const double tol = c->opts.tol * c->sigma;
+  for (;;) {
+    for (int j = j0; j < m; j += B) {
+      apply_op(c, false, static_cast<char*>(c->V) + (size_t)j * vs, c->ldv, 1, c->U, 4, 1, B);
+      launch_orth(c->orth, c->vt, j + B, j, B, s);
+      matvecs += B;
+    }
+    check_cuda(cudaMemcpyAsync(c->Hh, c->Hd, sizeof(double) * ldh * m, cudaMemcpyDeviceToHost, s), "d2h");
+    check_err_word(c);  // synchronises
+    // symmetric projected matrix from the upper triangle
+    for (int jj = 0; jj < m; ++jj)
+      for (int ii = 0; ii <= jj; ++ii) {
+        const double v = c->Hh[(size_t)jj * ldh + ii];
+        T[(size_t)jj * m + ii] = v;
+        T[(size_t)ii * m + jj] = v;
+      }
+    host_symmetric_eig(m, T.data(), theta.data());
+    // residual norms ||H[m:m+B, 0:m] y_i||
+    for (int i = 0; i < m; ++i) {
+      double acc = 0.0;
+      for (int r = 0; r < B; ++r) {
+        double sr = 0.0;
+        for (int q = 0; q < m; ++q) sr += c->Hh[(size_t)q * ldh + m + r] * T[(size_t)i * m + q];
+        acc += sr * sr;
+      }
+      resid[i] = std::sqrt(acc);
+    }
+    int nconv = 0;
+    for (int i = 0; i < k; ++i) nconv += resid[i] <= tol;
+    if (nconv == k || restarts >= c->opts.max_restarts) {
+      converged = nconv == k;
+      break;
+    }
+    int K = k + (m - k) / 2;
+    K = std::min(K, m - B);
+    K = std::max(K / B * B, ((k + B - 1) / B) * B);
+    if (K > m - B) K = m - B;
+    for (int i = 0; i < K; ++i)
+      for (int q = 0; q < m; ++q) c->Yh[(size_t)i * m + q] = T[(size_t)i * m + q];
+    check_cuda(cudaMemcpyAsync(c->Yd, c->Yh, sizeof(double) * m * K, cudaMemcpyHostToDevice, s), "h2d");
+    launch_restart(c->vt, n, c->V, c->ldv, m, K, B, c->Yd, s);
+    // new projected matrix: diag(theta) plus the coupling rows of the carried block
+    std::vector<double> Hn((size_t)ldh * m, 0.0);
+    for (int i = 0; i < K; ++i) Hn[(size_t)i * ldh + i] = theta[i];
+    for (int r = 0; r < B; ++r)
+      for (int i = 0; i < K; ++i) {
+        double sr = 0.0;
+        for (int q = 0; q < m; ++q) sr += c->Hh[(size_t)q * ldh + m + r] * T[(size_t)i * m + q];
+        Hn[(size_t)i * ldh + K + r] = sr;
+      }
+    std::memcpy(c->Hh, Hn.data(), sizeof(double) * ldh * m);
+    check_cuda(cudaMemcpyAsync(c->Hd, c->Hh, sizeof(double) * ldh * m, cudaMemcpyHostToDevice, s), "h2d");
+    j0 = K;
+    ++restarts;
+  }
+  // Ritz vectors X = V Y[:, 0:k]
+  for (int i = 0; i < k; ++i)
+    for (int q = 0; q < m; ++q) c->Yh[(size_t)i * m + q] = T[(size_t)i * m + q];
+  check_cuda(cudaMemcpyAsync(c->Yd, c->Yh, sizeof(double) * m * k, cudaMemcpyHostToDevice, s), "h2d");
+  launch_restart(c->vt, n, c->V, c->ldv, m, k, B, c->Yd, s);
+  launch_to_f64(c->vt, n, c->V, c->ldv, k, c->X64, s);
+  // FP64 Rayleigh quotients and residuals with the FP64 operator
+  for (int i = 0; i < k; i += 4) {
+    const int nv = std::min(4, k - i);
+    apply_op(c, true, c->X64 + (size_t)i * n, 1, n, c->AX64 + (size_t)i * n, 1, n, nv);
+  }
+  launch_column_stats(n, k, c->X64, c->AX64, nullptr, c->stat_partial, c->stat_blocks, nullptr, s);
+  std::vector<double> st((size_t)c->stat_blocks * k * 3);
+  check_cuda(cudaMemcpyAsync(st.data(), c->stat_partial, st.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "d2h");
+  check_err_word(c);
+  std::vector<double> xay(k, 0.0), xx(k, 0.0), ayay(k, 0.0);
+  for (int b = 0; b < c->stat_blocks; ++b)
+    for (int i = 0; i < k; ++i) {
+      xay[i] += st[((size_t)b * k + i) * 3 + 0];
+      xx[i] += st[((size_t)b * k + i) * 3 + 1];
+      ayay[i] += st[((size_t)b * k + i) * 3 + 2];
+    }
+  c->lam_h.assign(k, 0.0);
+  double maxres = 0.0;
+  for (int i = 0; i < k; ++i) {
+    const double lam = xay[i] / xx[i];
+    c->lam_h[i] = lam;
+    const double r2 = std::max(0.0, (ayay[i] - 2.0 * lam * xay[i] + lam * lam * xx[i]) / xx[i]);
+    maxres = std::max(maxres, std::sqrt(r2) / c->sigma);
+  }
+  // order by Rayleigh quotient (they are Ritz-ordered already up to rounding)
+  std::vector<int> ord(k);
+  for (int i = 0; i < k; ++i) ord[i] = i;
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return c->lam_h[a] < c->lam_h[b]; });
+  bool perm = false;
+  for (int i = 0; i < k; ++i) perm |= ord[i] != i;
+  if (perm) {
+    check_cuda(cudaMemcpyAsync(c->AX64, c->X64, sizeof(double) * n * k, cudaMemcpyDeviceToDevice, s), "d2d");
+    for (int i = 0; i < k; ++i)
+      check_cuda(cudaMemcpyAsync(c->X64 + (size_t)i * n, c->AX64 + (size_t)ord[i] * n, sizeof(double) * n,
+                                 cudaMemcpyDeviceToDevice, s), "d2d");
+    std::vector<double> l2(k), x2(k);
+    for (int i = 0; i < k; ++i) {
+      l2[i] = c->lam_h[ord[i]];
+      x2[i] = xx[ord[i]];
+    }
+    c->lam_h = l2;
+    xx = x2;
+  }
+  inf.ms_solve = tsolve.stop(s);
+  inf.restarts = restarts;
+  inf.matvecs = matvecs;
+  inf.max_resid = maxres;
+  int status = converged && maxres <= c->opts.tol * 1.0000001 ? SFAIRSC_OK : SFAIRSC_ERR_NOT_CONVERGED;
+  if (converged && maxres > c->opts.tol) status = SFAIRSC_ERR_NOT_CONVERGED;
+  for (int i = 0; i < k; ++i)
+    if (c->lam_h[i] >= c->sigma * (1.0 - 1e-8)) status = SFAIRSC_ERR_SHIFT;
+  // unit-norm columns in FP64, then H = D^{-1/2} X with the sign convention
+  {
+    std::vector<double> scale(k);
+    for (int i = 0; i < k; ++i) scale[i] = 1.0 / std::sqrt(xx[i]);
+    check_cuda(cudaMemcpyAsync(c->AX64, scale.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s), "h2d");
+    launch_scale_columns(n, k, c->X64, c->AX64, s);
+    check_cuda(cudaStreamSynchronize(s), "sync");
+  }
+  launch_embed(n, k, c->X64, c->dinv64, c->normalized, c->Hres, c->colkey, s);
+  check_cuda(cudaMemcpyAsync(c->lam_d, c->lam_h.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s), "h2d");
+  // diagnostics: max |F^T H| and max |H^T D H - I|
+  {
+    const int h = c->h;
+    launch_diagnostics(n, k, h, c->Hres, c->deg, c->lab, c->params, c->diag_partial, c->diag_blocks, nullptr, s);
+    const size_t P = (size_t)h * k + (size_t)k * k;
+    std::vector<double> dg((size_t)c->diag_blocks * P);
+    check_cuda(cudaMemcpyAsync(dg.data(), c->diag_partial, dg.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "d2h");
+    check_cuda(cudaStreamSynchronize(s), "diagnostics");
+    std::vector<double> acc(P, 0.0);
+    for (int b = 0; b < c->diag_blocks; ++b)
+      for (size_t i = 0; i < P; ++i) acc[i] += dg[(size_t)b * P + i];
+    double ferr = 0.0, derr = 0.0;
+    for (int i = 0; i < k; ++i) {
+      double tot = 0.0;
+      for (int g = 0; g < h; ++g) tot += acc[(size_t)g * k + i];
+      for (int g = 0; g + 1 < h; ++g) ferr = std::max(ferr, std::fabs(acc[(size_t)g * k + i] - c->z[g] * tot));
+    }
+    for (int a = 0; a < k; ++a)
+      for (int b = a; b < k; ++b) {
+        const double v = acc[(size_t)h * k + (size_t)a * k + b];
+        derr = std::max(derr, std::fabs(v - (a == b ? 1.0 : 0.0)));
+      }
+    inf.fairness_err = ferr;
+    inf.dorth_err = derr;
+  }
+  if (eigenvalues) {
+    if (is_device_ptr(eigenvalues))
+      check_cuda(cudaMemcpyAsync(eigenvalues, c->lam_d, sizeof(double) * k, cudaMemcpyDeviceToDevice, s), "copy");
+    else
+      std::memcpy(eigenvalues, c->lam_h.data(), sizeof(double) * k);
+  }
+  if (Hout)
+    check_cuda(cudaMemcpyAsync(Hout, c->Hres, sizeof(double) * n * k,
+                               is_device_ptr(Hout) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s), "copy H");
+  if (labels) {
+    Timer tk(s);
+    const KmeansResult kr = run_kmeans(n, k, c->Hres, k, c->opts.kmeans_seed, c->opts.kmeans_n_init,
+                                       c->opts.kmeans_max_iter, c->labels_d, nullptr, s);
+    inf.kmeans_inertia = kr.inertia;
+    inf.kmeans_iters = kr.iterations;
+    check_cuda(cudaMemcpyAsync(labels, c->labels_d, sizeof(int32_t) * n,
+                               is_device_ptr(labels) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s), "copy labels");
+    inf.ms_kmeans = tk.stop(s);
+  }
+  check_cuda(cudaStreamSynchronize(s), "solve end");
+  c->solved = true;
+  inf.status = status;
+  inf.ms_total = inf.ms_solve + inf.ms_kmeans;
+  if (info) *info = inf;
+  return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sfairsc_strerror(int status) {
+  switch (status) {
+    case SFAIRSC_OK: return "ok";
+    case SFAIRSC_ERR_INVALID_ARG: return "invalid argument";
+    case SFAIRSC_ERR_BAD_CSR: return "invalid CSR structure";
+    case SFAIRSC_ERR_ISOLATED_VERTEX: return "isolated vertex (zero degree)";
+    case SFAIRSC_ERR_EMPTY_GROUP: return "empty group";
+    case SFAIRSC_ERR_K_TOO_LARGE: return "k too large for the graph";
+    case SFAIRSC_ERR_NONFINITE: return "non-finite input";
+    case SFAIRSC_ERR_NOT_CONVERGED: return "eigensolver did not converge";
+    case SFAIRSC_ERR_SHIFT: return "shift sigma not above the wanted eigenvalues";
+    case SFAIRSC_ERR_CUDA: return "CUDA error";
+    case SFAIRSC_ERR_OOM: return "out of memory";
+    case SFAIRSC_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
+    case SFAIRSC_ERR_UNSUPPORTED: return "unsupported configuration";
+    case SFAIRSC_ERR_BREAKDOWN: return "Krylov block lost rank";
+    default: return "unknown status";
+  }
+}
+
+const char* sfairsc_last_error(void) { return g_last_error.c_str(); }
+
+int sfairsc_opts_default(sfairsc_opts* o) {
+  if (!o) return SFAIRSC_ERR_INVALID_ARG;
+  std::memset(o, 0, sizeof(*o));
+  o->sigma = std::numeric_limits<double>::quiet_NaN();
+  o->tol = 1e-6;
+  o->max_restarts = 200;
+  o->basis = 0;
+  o->prec = SFAIRSC_PREC_MIXED;
+  o->block = 1;
+  o->seed = 1;
+  o->kmeans_seed = 0;
+  o->kmeans_n_init = 1;
+  o->kmeans_max_iter = 100;
+  o->validate = 1;
+  return SFAIRSC_OK;
+}
+
+int sfairsc_create(sfairsc_ctx** out, int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
+                   const void* values, int32_t value_dtype, const int32_t* group_labels, int32_t h, int32_t k,
+                   int32_t normalized, const sfairsc_opts* opts, void* cuda_stream) {
+  if (!out) return SFAIRSC_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n < 2 || n > (1ll << 30) || nnz < 1 || nnz > 0x7fffffffll || !row_ptr || !col_idx || !values || !group_labels ||
+      h < 1 || k < 1 || (value_dtype != SFAIRSC_F64 && value_dtype != SFAIRSC_F32 && value_dtype != SFAIRSC_BF16)) {
+    g_last_error = "invalid argument to sfairsc_create";
+    return SFAIRSC_ERR_INVALID_ARG;
+  }
+  if (h > SFAIRSC_MAX_GROUPS) {
+    g_last_error = "h exceeds 32 groups";
+    return SFAIRSC_ERR_UNSUPPORTED;
+  }
+  std::unique_ptr<sfairsc_ctx> c(new (std::nothrow) sfairsc_ctx());
+  if (!c) return SFAIRSC_ERR_OOM;
+  sfairsc_opts_default(&c->opts);
+  if (opts) c->opts = *opts;
+  if (!(c->opts.tol > 0.0) || c->opts.max_restarts < 0 || c->opts.block < 1 || c->opts.block > SFAIRSC_MAX_BLOCK ||
+      c->opts.kmeans_n_init < 1 || c->opts.kmeans_max_iter < 1 || (c->opts.prec != 0 && c->opts.prec != 1)) {
+    g_last_error = "invalid options";
+    return SFAIRSC_ERR_INVALID_ARG;
+  }
+  c->n = n;
+  c->nnz = nnz;
+  c->h = h;
+  c->k = k;
+  c->normalized = normalized ? 1 : 0;
+  c->vdt_orig = value_dtype;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->vt = c->opts.prec == SFAIRSC_PREC_FP64 ? VecType::F64 : VecType::F32;
+  const int rc = guarded([&] { build_context(c.get(), row_ptr, col_idx, values, group_labels); });
+  if (rc != SFAIRSC_OK) return rc;
+  *out = c.release();
+  return SFAIRSC_OK;
+}
+
+int sfairsc_destroy(sfairsc_ctx* ctx) {
+  if (!ctx) return SFAIRSC_OK;
+  cudaStreamSynchronize(ctx->stream);
+  delete ctx;
+  return SFAIRSC_OK;
+}
+
+int sfairsc_get_sigma(const sfairsc_ctx* ctx, double* sigma) {
+  if (!ctx || !sigma) return SFAIRSC_ERR_INVALID_ARG;
+  *sigma = ctx->sigma;
+  return SFAIRSC_OK;
+}
+
+int sfairsc_apply_operator(sfairsc_ctx* ctx, const void* w, void* out, int32_t nvec) {
+  if (!ctx || !w || !out || nvec < 1 || nvec > SFAIRSC_MAX_BLOCK) return SFAIRSC_ERR_INVALID_ARG;
+  return guarded([&] {
+    const size_t vs = ctx->vt == VecType::F64 ? 8 : 4;
+    const size_t bytes = (size_t)ctx->n * nvec * vs;
+    const bool wd = is_device_ptr(w), od = is_device_ptr(out);
+    const void* win = w;
+    void* wout = out;
+    void* tmp_in = nullptr;
+    void* tmp_out = nullptr;
+    if (!wd) {
+      check_cuda(cudaMallocAsync(&tmp_in, bytes, ctx->stream), "allocation");
+      check_cuda(cudaMemcpyAsync(tmp_in, w, bytes, cudaMemcpyHostToDevice, ctx->stream), "h2d");
+      win = tmp_in;
+    }
+    if (!od) {
+      check_cuda(cudaMallocAsync(&tmp_out, bytes, ctx->stream), "allocation");
+      wout = tmp_out;
+    }
+    apply_op(ctx, false, win, 1, ctx->n, wout, 1, ctx->n, nvec);
+    if (!od) check_cuda(cudaMemcpyAsync(out, tmp_out, bytes, cudaMemcpyDeviceToHost, ctx->stream), "d2h");
+    if (tmp_in) cudaFreeAsync(tmp_in, ctx->stream);
+    if (tmp_out) cudaFreeAsync(tmp_out, ctx->stream);
+    if (!wd || !od) check_err_word(ctx);
+  });
+}
+
+int sfairsc_solve(sfairsc_ctx* ctx, double* eigenvalues, double* H, int32_t* labels, sfairsc_info* info) {
+  if (!ctx) return SFAIRSC_ERR_INVALID_ARG;
+  int status = SFAIRSC_OK;
+  const int rc = guarded([&] { status = solve_impl(ctx, eigenvalues, H, labels, info); });
+  if (rc != SFAIRSC_OK) {
+    if (info) info->status = rc;
+    return rc;
+  }
+  return status;
+}
+
+int sfairsc_kmeans(int64_t n, int32_t d, const double* X, int32_t kc, uint64_t seed, int32_t n_init, int32_t max_iter,
+                   int32_t* labels, double* centroids, double* inertia, int32_t* iterations, void* cuda_stream) {
+  if (!X || !labels || n < 1 || d < 1 || kc < 1 || kc > n || n_init < 1 || max_iter < 1) return SFAIRSC_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  return guarded([&] {
+    std::vector<void*> tmp;
+    auto dev = [&](size_t bytes) {
+      void* p = nullptr;
+      check_cuda(cudaMallocAsync(&p, std::max<size_t>(bytes, 1), s), "allocation");
+      tmp.push_back(p);
+      return p;
+    };
+    const double* Xd = X;
+    if (!is_device_ptr(X)) {
+      void* p = dev(sizeof(double) * n * d);
+      check_cuda(cudaMemcpyAsync(p, X, sizeof(double) * n * d, cudaMemcpyHostToDevice, s), "h2d");
+      Xd = static_cast<const double*>(p);
+    }
+    const bool ld = is_device_ptr(labels);
+    int32_t* Ld = ld ? labels : static_cast<int32_t*>(dev(sizeof(int32_t) * n));
+    const bool cd = centroids && is_device_ptr(centroids);
+    double* Cd = centroids ? (cd ? centroids : static_cast<double*>(dev(sizeof(double) * kc * d))) : nullptr;
+    const KmeansResult r = run_kmeans(n, d, Xd, kc, seed, n_init, max_iter, Ld, Cd, s);
+    if (!ld) check_cuda(cudaMemcpyAsync(labels, Ld, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s), "d2h");
+    if (centroids && !cd) check_cuda(cudaMemcpyAsync(centroids, Cd, sizeof(double) * kc * d, cudaMemcpyDeviceToHost, s), "d2h");
+    check_cuda(cudaStreamSynchronize(s), "k-means");
+    for (void* p : tmp) cudaFreeAsync(p, s);
+    check_cuda(cudaStreamSynchronize(s), "k-means free");
+    if (inertia) *inertia = r.inertia;
+    if (iterations) *iterations = r.iterations;
+  });
+}
+
+int sfairsc_backward(sfairsc_ctx* ctx, const double* grad_lambda, double* grad_values, double bandwidth,
+                     double* grad_bandwidth) {
+  if (!ctx || !grad_lambda || !grad_values) return SFAIRSC_ERR_INVALID_ARG;
+  if (!ctx->solved) {
+    g_last_error = "sfairsc_backward needs a prior sfairsc_solve";
+    return SFAIRSC_ERR_INVALID_ARG;
+  }
+  return guarded([&] {
+    cudaStream_t s = ctx->stream;
+    const int k = ctx->k;
+    std::vector<void*> tmp;
+    const double* gd = grad_lambda;
+    if (!is_device_ptr(grad_lambda)) {
+      void* p = nullptr;
+      check_cuda(cudaMallocAsync(&p, sizeof(double) * k, s), "allocation");
+      tmp.push_back(p);
+      check_cuda(cudaMemcpyAsync(p, grad_lambda, sizeof(double) * k, cudaMemcpyHostToDevice, s), "h2d");
+      gd = static_cast<const double*>(p);
+    }
+    const bool od = is_device_ptr(grad_values);
+    double* G = grad_values;
+    if (!od) {
+      void* p = nullptr;
+      check_cuda(cudaMallocAsync(&p, sizeof(double) * ctx->nnz, s), "allocation");
+      tmp.push_back(p);
+      G = static_cast<double*>(p);
+    }
+    const double bw = grad_bandwidth ? bandwidth : 0.0;
+    launch_backward((int)ctx->n, ctx->row_ptr, ctx->col, ctx->val_orig, ctx->vdt_orig, k, ctx->Hres, ctx->lam_d, gd, G,
+                    bw, ctx->bw_partial, ctx->bw_blocks, ctx->bw_A, s);
+    if (!od) check_cuda(cudaMemcpyAsync(grad_values, G, sizeof(double) * ctx->nnz, cudaMemcpyDeviceToHost, s), "d2h");
+    std::vector<double> part(ctx->bw_blocks);
+    check_cuda(cudaMemcpyAsync(part.data(), ctx->bw_partial, sizeof(double) * ctx->bw_blocks, cudaMemcpyDeviceToHost, s),
+               "d2h");
+    check_cuda(cudaStreamSynchronize(s), "backward");
+    for (void* p : tmp) cudaFreeAsync(p, s);
+    if (grad_bandwidth) {
+      double acc = 0.0;
+      for (double v : part) acc += v;
+      *grad_bandwidth = bw > 0.0 ? acc : 0.0;
+    }
+    check_cuda(cudaStreamSynchronize(s), "backward end");
+  });
+}
+
+}  // extern "C"

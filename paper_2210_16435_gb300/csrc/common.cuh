@@ -1,0 +1,153 @@
+// Device helpers shared by the s-FairSC kernels: value/vector type traits,
+// a bounded grid barrier, warp reductions, and error-free FP32 transforms.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sfairsc {
+
+constexpr int kWarp = 32;
+constexpr int kMaxGroups = 32;
+
+// Error bits written by kernels into the context's device error word.
+enum : unsigned {
+  kErrBarrierTimeout = 1u << 0,
+  kErrBreakdown = 1u << 1,
+  kErrNonFinite = 1u << 2,
+};
+
+// ---------------------------------------------------------------- load helpers
+__device__ __forceinline__ double to_f64(double v) { return v; }
+__device__ __forceinline__ double to_f64(float v) { return (double)v; }
+__device__ __forceinline__ double to_f64(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+__device__ __forceinline__ float to_f32(double v) { return (float)v; }
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename VT>
+__device__ __forceinline__ VT cvt(double v);
+template <>
+__device__ __forceinline__ double cvt<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ float cvt<float>(double v) { return (float)v; }
+
+template <typename VT, typename MT>
+__device__ __forceinline__ VT val_as(MT v);
+template <>
+__device__ __forceinline__ double val_as<double, double>(double v) { return v; }
+template <>
+__device__ __forceinline__ double val_as<double, float>(float v) { return (double)v; }
+template <>
+__device__ __forceinline__ double val_as<double, __nv_bfloat16>(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+template <>
+__device__ __forceinline__ float val_as<float, double>(double v) { return (float)v; }
+template <>
+__device__ __forceinline__ float val_as<float, float>(float v) { return v; }
+template <>
+__device__ __forceinline__ float val_as<float, __nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// ---------------------------------------------------------------- warp sums
+template <typename T>
+__device__ __forceinline__ T warp_allsum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    T u = __shfl_xor_sync(0xffffffffu, v, o);
+    v = u > v ? u : v;
+  }
+  return v;
+}
+
+// ---------------------------------------------------------------- error-free transforms
+// TwoSum (Knuth) and TwoProd (FMA): s + e == a + b and p + e == a * b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Compensated dot-product accumulator (Ogita, Rump and Oishi, "Accurate sum
+// and dot product", 2005, Algorithm Dot2): the result is as accurate as if
+// computed in twice the working precision and then rounded.
+struct Dot2 {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    float p = __fmul_rn(a, b);
+    float pe = __fmaf_rn(a, b, -p);
+    float t, e;
+    two_sum(s, p, t, e);
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(pe, e));
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// Nanosecond global timer (PTX %globaltimer).
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// ---------------------------------------------------------------- grid barrier
+// Sense-by-generation barrier over all CTAs of a cooperative launch.  The
+// spin is bounded: after `limit_ns` nanoseconds the waiting CTA sets
+// kErrBarrierTimeout in *err and the barrier returns false, so no launch can
+// hang.  Co-residency of all CTAs is guaranteed by the cooperative launch.
+struct GridBarrier {
+  unsigned* count;       // arrivals in the current generation
+  unsigned* generation;  // incremented by the last arriver
+};
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned atom_add_acqrel_gpu(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+__device__ __forceinline__ bool grid_sync(GridBarrier bar, unsigned* err, unsigned long long limit_ns = 2000000000ull) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    unsigned gen = ld_acquire_gpu(bar.generation);
+    __threadfence();
+    unsigned arrived = atom_add_acqrel_gpu(bar.count, 1u);
+    if (arrived == gridDim.x * gridDim.y * gridDim.z - 1) {
+      *bar.count = 0u;
+      __threadfence();
+      st_release_gpu(bar.generation, gen + 1u);
+    } else {
+      unsigned long long t0 = globaltimer_ns();
+      while (ld_acquire_gpu(bar.generation) == gen) {
+        __nanosleep(64);
+        if (globaltimer_ns() - t0 > limit_ns) {
+          atomicOr(err, kErrBarrierTimeout);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+}  // namespace sfairsc

@@ -1,0 +1,137 @@
+// Internal declarations of the s-FairSC library: the context, parameter
+// layout and the host-side launchers of every kernel.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sfairsc.h"
+
+namespace sfairsc {
+
+// Device parameter block (doubles): z_s, the Cholesky factor of C^T C and sigma.
+constexpr int kPZ = 0;                 // z_s = |V_s| / n, s < 32
+constexpr int kPL = 32;                // lower Cholesky factor of C^T C, row-major, stride 31
+constexpr int kLStride = 31;
+constexpr int kPSigma = kPL + 31 * 31; // sigma
+constexpr int kParams = 1024;
+
+enum class VecType { F64 = 0, F32 = 1 };
+
+struct CudaError {
+  cudaError_t err;
+  const char* what;
+};
+
+// Throwing wrappers used inside the library; the C entry points catch and map to status codes.
+struct Status {
+  int code;
+  std::string msg;
+};
+void check_cuda(cudaError_t e, const char* what);
+[[noreturn]] void fail(int code, const std::string& msg);
+
+// Operator launch description (everything the fused kernel needs).
+struct OpPlan {
+  int n = 0;
+  int h = 1;
+  int normalized = 1;
+  int grid = 0;          // cooperative CTAs
+  int threads = 1024;
+  int lanes_per_row = 8; // sub-warp width for the SpMV
+  const int32_t* row_ptr = nullptr;
+  const int32_t* col = nullptr;
+  const void* val = nullptr;
+  int val_dtype = 0;
+  const uint8_t* lab = nullptr;
+  const void* dinv = nullptr;  // VT[n]
+  const double* deg = nullptr; // double[n] (unnormalized path)
+  const double* params = nullptr;
+  void* ytil = nullptr;        // VT[n * 4]
+  double* partial = nullptr;   // double[grid * 32 * 4]
+  const int32_t* cta_rows = nullptr;  // int32[grid + 1]
+  unsigned* barrier = nullptr; // 2 words
+  unsigned* err = nullptr;
+};
+
+// Launch out = L_n^sigma w for nvec vectors; element (r, v) of w is w[r*wrs + v*wcs]
+// and of out is out[r*ors + v*ocs].
+void launch_operator(const OpPlan& p, VecType vt, const void* w, int64_t wrs, int64_t wcs, void* out, int64_t ors,
+                     int64_t ocs, int nvec, cudaStream_t s);
+// Largest co-resident grid of the operator kernel for this instantiation.
+int operator_max_grid(VecType vt, int val_dtype, int nvec, int threads, size_t smem);
+size_t operator_smem_bytes(int threads, int h, int nvec, VecType vt);
+
+// Setup kernels.
+void launch_validate(int n, int64_t nnz, const int32_t* row_ptr, const int32_t* col, const void* val, int val_dtype,
+                     const int32_t* labels, int h, int check_symmetry, unsigned* flags, cudaStream_t s);
+void launch_degrees(int n, const int32_t* row_ptr, const void* val, int val_dtype, const int32_t* labels_in,
+                    uint8_t* lab, double* deg, double* dinv64, float* dinv32, double* blocksums, int nblocks,
+                    int h, int normalized, unsigned* flags, cudaStream_t s);
+int degrees_blocks(int n);
+void launch_sigma_rows(int n, const int32_t* row_ptr, const int32_t* col, const void* val, int val_dtype,
+                       const double* dinv64, const double* deg, int normalized, double* blockmax, int nblocks,
+                       cudaStream_t s);
+void launch_row_partition(int n, const int32_t* row_ptr, int grid, int row_weight, int32_t* cta_rows, cudaStream_t s);
+
+// Krylov kernels.
+struct OrthPlan {
+  int n = 0;
+  int grid = 0;
+  int threads = 1024;
+  int64_t ldv = 0;
+  void* V = nullptr;          // VT, n x ldv columns
+  void* U = nullptr;          // VT, n x B, column-major with ld ldv
+  double* H = nullptr;        // projected matrix, column-major, ld ldh
+  int ldh = 0;
+  double* partial = nullptr;  // grid * (mmax + 4) * 4
+  double* coef = nullptr;     // (mmax + 4) * 4 reduced coefficients
+  const int32_t* cta_rows = nullptr;
+  unsigned* barrier = nullptr;
+  unsigned* err = nullptr;
+};
+// Orthogonalise the B columns in U against V[:, 0:J] (CGS2), record the
+// coefficients in H[0:J, j:j+B], orthonormalise the block (CholQR), store it
+// as V[:, J:J+B] and its R factor in H[J:J+B, j:j+B].
+void launch_orth(const OrthPlan& p, VecType vt, int J, int j, int B, cudaStream_t s);
+int orth_max_grid(VecType vt, int B, int threads);
+// V[:, 0:K] = V[:, 0:m] Y (Y: m x K column-major FP64 on device), then V[:, K:K+B] = V[:, m:m+B].
+void launch_restart(VecType vt, int n, void* V, int64_t ldv, int m, int K, int B, const double* Y, cudaStream_t s);
+// Fill V[:, 0:B] with a seeded pseudo-random block.
+void launch_random_block(VecType vt, int n, void* V, int64_t ldv, int B, uint64_t seed, cudaStream_t s);
+// FP64 copy / conversion of the first k columns of V to X64 (n x k column-major).
+void launch_to_f64(VecType vt, int n, const void* V, int64_t ldv, int k, double* X, cudaStream_t s);
+// Column norms and Rayleigh data: out[c] = <X_c, AX_c>, out[k + c] = <X_c, X_c>, out[2k + c] = ||AX_c - l_c X_c||^2.
+void launch_column_stats(int n, int k, const double* X, const double* AX, const double* lam, double* partial,
+                         int nblocks, double* out, cudaStream_t s);
+// X[:, c] *= scale[c] (X column-major n x k).
+void launch_scale_columns(int n, int k, double* X, const double* scale, cudaStream_t s);
+// Embedding H = D^{-1/2} X (row-major n x k), sign per column; sign_partial workspace.
+void launch_embed(int n, int k, const double* X, const double* dinv64, int normalized, double* H,
+                  unsigned long long* colkey, cudaStream_t s);
+// Fairness and D-orthogonality diagnostics of H.
+void launch_diagnostics(int n, int k, int h, const double* H, const double* deg, const uint8_t* lab,
+                        const double* params, double* partial, int nblocks, double* out, cudaStream_t s);
+
+// Backward SDDMM.
+// grad[e] for every stored entry; partial[b] = per-block sum of the bandwidth terms; A = n-vector workspace.
+void launch_backward(int n, const int32_t* row_ptr, const int32_t* col, const void* val, int val_dtype, int k,
+                     const double* H, const double* lam, const double* gbar, double* grad, double bandwidth,
+                     double* partial, int nblocks, double* A, cudaStream_t s);
+
+// k-means (device part).  Returns inertia and iterations of the winner.
+struct KmeansResult {
+  double inertia = 0.0;
+  int iterations = 0;
+};
+KmeansResult run_kmeans(int64_t n, int d, const double* X, int kc, uint64_t seed, int n_init, int max_iter,
+                        int32_t* labels, double* centroids, cudaStream_t s);
+
+// Host FP64 symmetric eigensolver (Householder tridiagonalisation + implicit QL).
+// A: m x m column-major symmetric (overwritten with eigenvectors), w: eigenvalues ascending.
+void host_symmetric_eig(int m, double* A, double* w);
+
+}  // namespace sfairsc

@@ -1,0 +1,133 @@
+"""PyTorch-facing wrapper: tensors in, tensors out; all work in libsfairsc.so.
+
+PyTorch provides device memory and the stream; every computation is a call
+into the C ABI (see include/sfairsc.h).
+"""
+from __future__ import annotations
+
+import torch
+
+from . import binding as B
+
+_DTYPES = {torch.float64: B.SFAIRSC_F64, torch.float32: B.SFAIRSC_F32, torch.bfloat16: B.SFAIRSC_BF16}
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else t.data_ptr()
+
+
+class FairSC:
+    """One graph's s-FairSC context (Algorithm 3).
+
+    row_ptr, col_idx: int32 CSR of the symmetric weight matrix W (both triangles);
+    values: float64 / float32 / bfloat16 weights; groups: int32 labels in [0, h).
+    Tensors may live on the GPU (borrowed: keep them alive) or the CPU (copied).
+    """
+
+    def __init__(self, row_ptr, col_idx, values, groups, k: int, h: int | None = None, normalized: bool = True,
+                 prec: str = "mixed", block: int = 1, tol: float = 1e-6, basis: int = 0, max_restarts: int = 200,
+                 sigma: float | None = None, seed: int = 1, kmeans_seed: int = 0, kmeans_n_init: int = 1,
+                 kmeans_max_iter: int = 100, validate: int = 1, stream: torch.cuda.Stream | None = None):
+        self._keep = [t.contiguous() for t in (row_ptr, col_idx, values, groups)]
+        row_ptr, col_idx, values, groups = self._keep
+        if row_ptr.dtype != torch.int32 or col_idx.dtype != torch.int32 or groups.dtype != torch.int32:
+            raise TypeError("row_ptr, col_idx and groups must be int32")
+        if values.dtype not in _DTYPES:
+            raise TypeError("values must be float64, float32 or bfloat16")
+        self.n = row_ptr.numel() - 1
+        self.nnz = col_idx.numel()
+        self.k = int(k)
+        self.h = int(h) if h is not None else int(groups.max().item()) + 1
+        self.prec = prec
+        self.vec_dtype = torch.float64 if prec == "fp64" else torch.float32
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        opts = B.make_opts(prec, block, tol, basis, max_restarts, sigma, seed, kmeans_seed, kmeans_n_init,
+                           kmeans_max_iter, validate)
+        self.ctx = B.sfairsc_create(self.n, self.nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(values), _DTYPES[values.dtype],
+                                    _ptr(groups), self.h, self.k, 1 if normalized else 0, opts,
+                                    self.stream.cuda_stream)
+        self.sigma = B.sfairsc_get_sigma(self.ctx)
+        self.info = None
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            B.sfairsc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply_operator(self, w: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """L_n^sigma w for w of shape (n,) or (n, b), b <= 4 (Sec. 3.4 (i))."""
+        vec = w.dim() == 1
+        W = w.reshape(self.n, -1)
+        nv = W.shape[1]
+        Wc = W.t().contiguous().to(self.vec_dtype)  # column-major: each vector contiguous
+        O = torch.empty_like(Wc) if out is None else out.view(nv, self.n)
+        B.sfairsc_apply_operator(self.ctx, _ptr(Wc), _ptr(O), nv)
+        res = O.t()
+        return res.reshape(-1) if vec else res
+
+    def solve(self, want_labels: bool = True, allow_not_converged: bool = False, on_host: bool = False):
+        """Eigenvalues (k,), H (n, k) and labels (n,) plus the info dict."""
+        dev = torch.device("cpu") if on_host else self.device
+        lam = torch.empty(self.k, dtype=torch.float64, device=dev)
+        H = torch.empty(self.n, self.k, dtype=torch.float64, device=dev)
+        lab = torch.empty(self.n, dtype=torch.int32, device=dev) if want_labels else None
+        if on_host:
+            lam, H = lam.pin_memory(), H.pin_memory()
+            lab = lab.pin_memory() if lab is not None else None
+        allow = (0, -7) if allow_not_converged else (0,)
+        rc, info = B.sfairsc_solve(self.ctx, _ptr(lam), _ptr(H), _ptr(lab), allow)
+        self.info = info.as_dict()
+        self.status = rc
+        return lam, H, lab, self.info
+
+    def backward(self, grad_lambda: torch.Tensor, bandwidth: float | None = None):
+        """d(sum_i gbar_i lambda_i)/d values (nnz,) and optionally d/d bandwidth."""
+        g = grad_lambda.to(device=self.device, dtype=torch.float64).contiguous()
+        out = torch.empty(self.nnz, dtype=torch.float64, device=self.device)
+        gs = B.sfairsc_backward(self.ctx, _ptr(g), _ptr(out), bandwidth or 0.0, want_bandwidth=bandwidth is not None)
+        return out, gs
+
+
+def kmeans(H: torch.Tensor, k: int, seed: int = 0, n_init: int = 1, max_iter: int = 100):
+    """Seeded, exactly reproducible k-means on the rows of H (labels, centroids, inertia, iterations)."""
+    X = H.to(torch.float64).contiguous()
+    n, d = X.shape
+    lab = torch.empty(n, dtype=torch.int32, device=X.device)
+    cen = torch.empty(k, d, dtype=torch.float64, device=X.device)
+    stream = torch.cuda.current_stream().cuda_stream if X.is_cuda else None
+    inertia, iters = B.sfairsc_kmeans(n, d, _ptr(X), k, seed, n_init, max_iter, _ptr(lab), _ptr(cen), stream)
+    return lab, cen, inertia, iters
+
+
+class FairEigenvalueSum(torch.autograd.Function):
+    """lambda_1..lambda_k of the fair problem as a differentiable function of the edge weights.
+
+    forward(values, row_ptr, col_idx, groups, k, h, bandwidth, opts) -> eigenvalues (k,)
+    backward gives d/d values through the SDDMM kernel and, when bandwidth is
+    a tensor, d/d bandwidth for Gaussian weights w = exp(-r^2 / (2 s^2)).
+    """
+
+    @staticmethod
+    def forward(ctx, values, row_ptr, col_idx, groups, k, h, bandwidth=None, opts=None):
+        opts = dict(opts or {})
+        solver = FairSC(row_ptr, col_idx, values.detach(), groups, k, h, **opts)
+        lam, H, _, info = solver.solve(want_labels=False, allow_not_converged=True)
+        ctx.solver = solver
+        ctx.has_bw = isinstance(bandwidth, torch.Tensor)
+        ctx.bw = float(bandwidth) if ctx.has_bw else None
+        ctx.values_dtype = values.dtype
+        return lam
+
+    @staticmethod
+    def backward(ctx, grad_lam):
+        gv, gs = ctx.solver.backward(grad_lam, ctx.bw)
+        ctx.solver.close()
+        gbw = torch.tensor(gs, dtype=torch.float64, device=gv.device) if ctx.has_bw else None
+        return gv.to(ctx.values_dtype), None, None, None, None, None, gbw, None

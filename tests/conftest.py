@@ -20,3 +20,25 @@ def golden(name):
 
     with open(os.path.join(GOLDEN, name)) as f:
         return json.load(f)
+
+
+@pytest.fixture(scope="session")
+def built_lib():
+    from paper_2210_16435_gb300 import buildlib as _b
+
+    return _b.build()
+
+
+def to_dev(a, dtype, device="cuda"):
+    import numpy as np
+    import torch
+
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device=device)
+
+
+def graph_tensors(g, value_dtype=None, device="cuda"):
+    import torch
+
+    value_dtype = value_dtype or torch.float64
+    return (to_dev(g.row_ptr, torch.int32, device), to_dev(g.col_idx, torch.int32, device),
+            to_dev(g.values, value_dtype, device), to_dev(g.groups, torch.int32, device))

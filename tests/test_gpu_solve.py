@@ -1,0 +1,164 @@
+"""End-to-end s-FairSC solves (Algorithm 3) against the oracle."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import torch
+
+from conftest import graph_tensors
+from msbm import category_probabilities, cell_sizes_equal, configs, sample_msbm
+from oracle import fairsc, metrics, problem
+from oracle.kmeans import kmeans as oracle_kmeans
+from oracle.sfairsc import operator_from_graph, residual_norms, smallest_eigenpairs
+
+pytestmark = pytest.mark.gpu
+
+
+def principal_angle(A, B):
+    Qa, _ = np.linalg.qr(A)
+    Qb, _ = np.linalg.qr(B)
+    s = np.linalg.svd(Qa.T @ Qb, compute_uv=False)
+    return float(np.arccos(np.clip(s.min(), -1.0, 1.0)))
+
+
+def eig_rel_err(got, ref, sigma, tol):
+    """Relative error when lambda >= 1e-3 sigma, absolute (in units of sigma) below."""
+    big = np.abs(ref) >= 1e-3 * sigma
+    rel = np.where(big, np.abs(got - ref) / np.maximum(np.abs(ref), 1e-300), np.abs(got - ref) / sigma)
+    return rel.max()
+
+
+def solve_and_check(g, k, prec, block=1, lam_tol=None, normalized=True, ref=None, vdt=torch.float64):
+    from paper_2210_16435_gb300.solver import FairSC
+
+    rp, ci, v, gr = graph_tensors(g, vdt)
+    s = FairSC(rp, ci, v, gr, k=k, h=g.h, prec=prec, block=block, normalized=normalized)
+    lam, H, lab, info = s.solve()
+    lam, H, lab = lam.cpu().numpy(), H.cpu().numpy(), lab.cpu().numpy()
+    W = sp.csr_matrix((v.double().cpu().numpy(), g.col_idx, g.row_ptr), shape=(g.n, g.n))
+    op = operator_from_graph(g, normalized=normalized)
+    op.A = op.A  # same graph
+    if ref is None:
+        if g.n <= 2500:
+            lref, Href, Xref, _, _ = fairsc.sfairsc_dense(W, g.groups, g.h, k + 1, normalized=normalized)
+        else:
+            lref, Xref = smallest_eigenpairs(op, k + 1, tol=1e-13, method="eigsh")
+            d = problem.degrees(W)
+            Href = Xref / np.sqrt(d)[:, None] if normalized else Xref
+    else:
+        lref, Href = ref
+    lam_tol = lam_tol or (1e-6 if prec == "fp64" else 1e-4)
+    assert eig_rel_err(lam, lref[:k], op.sigma, lam_tol) <= lam_tol, (lam, lref[:k])
+    # residual with the oracle's FP64 operator on the returned H (X = D^{1/2} H)
+    d = problem.degrees(W)
+    X = H * np.sqrt(d)[:, None] if normalized else H
+    res = residual_norms(op, lam, X)
+    assert res.max() <= 1e-6 * op.sigma * 1.01, res.max() / op.sigma
+    # invariants: F^T H = 0 and H^T D H = I (eq. normal-prob-fair)
+    _, F, _ = problem.fairness_constraints(g.groups, g.h)
+    tol_inv = 1e-9 if prec == "fp64" else 1e-5
+    assert np.abs(F.T @ H).max() <= tol_inv * np.abs(H).sum(axis=0).max()
+    G = (H.T * d) @ H if normalized else H.T @ H
+    assert np.abs(G - np.eye(k)).max() <= tol_inv
+    # subspace: compare in the Euclidean-orthonormal X coordinates when the gap is clear
+    gap = lref[k] - lref[k - 1]
+    if gap > 100 * 1e-6 * op.sigma:
+        Xr = Href[:, :k] * np.sqrt(d)[:, None] if normalized else Href[:, :k]
+        ang = principal_angle(X, Xr)
+        assert ang <= 1e-4, ang
+    assert abs(info["sigma"] - op.sigma) <= 1e-12 * op.sigma
+    assert info["max_resid"] <= 1e-6
+    s.close()
+    return lam, H, lab, info
+
+
+def test_n2000_k5_h2_fp64(built_lib):
+    c = configs.msbm_n2000_k5_h2()
+    g = c["graph"]
+    lam, H, lab, info = solve_and_check(g, 5, "fp64")
+    # clusters: balance equal to the oracle's k-means on the oracle's embedding
+    W = g.to_scipy()
+    lref, Href, *_ = fairsc.sfairsc_dense(W, g.groups, 2, 5)
+    oref, _, _ = oracle_kmeans(Href, 5, seed=0, n_init=1, max_iter=100)
+    assert metrics.balance_multiset(lab, g.groups, 5, 2) == metrics.balance_multiset(oref, g.groups, 5, 2)
+    # and exactly the oracle's labels when the oracle clusters the library's own H
+    omine, _, _ = oracle_kmeans(H, 5, seed=0, n_init=1, max_iter=100)
+    assert np.array_equal(omine, lab)
+
+
+def test_n2000_k5_h2_mixed(built_lib):
+    g = configs.msbm_n2000_k5_h2()["graph"]
+    solve_and_check(g, 5, "mixed")
+
+
+@pytest.mark.parametrize("block", [2, 4])
+def test_block_lanczos(built_lib, block):
+    g = configs.msbm_n2000_k5_h2()["graph"]
+    solve_and_check(g, 5, "fp64", block=block)
+    solve_and_check(g, 5, "mixed", block=block)
+
+
+def test_n50k_shape_scaled(built_lib):
+    """The n = 50,000, k = 20, h = 5 workload's shape at n = 5,000."""
+    g = configs.msbm_n50k_k20_h5(scale=0.1)["graph"]
+    solve_and_check(g, 20, "mixed", vdt=torch.float32)
+    solve_and_check(g, 20, "fp64", vdt=torch.float32)
+
+
+def test_h1_plain_sc(built_lib):
+    cells = cell_sizes_equal(1500, 4, 1)
+    probs = category_probabilities(cells, 40, (0.7, 0.0, 0.3, 0.0))
+    g = sample_msbm(cells, probs, seed=3)
+    solve_and_check(g, 4, "fp64")
+
+
+def test_unnormalized_extension(built_lib):
+    cells = cell_sizes_equal(1200, 3, 3)
+    probs = category_probabilities(cells, 40, (0.5, 0.25, 0.15, 0.10))
+    g = sample_msbm(cells, probs, seed=4)
+    solve_and_check(g, 3, "fp64", normalized=False)
+
+
+def test_fair_cliques_exact_recovery(built_lib):
+    """Disjoint exactly-fair cliques joined weakly: k-means recovers them (Err = 0)."""
+    k, h, per = 4, 2, 50
+    n = k * per
+    clusters = np.repeat(np.arange(k), per)
+    groups = np.tile(np.arange(h), n // h)
+    W = (clusters[:, None] == clusters[None, :]).astype(float) - np.eye(n)
+    for c in range(k):
+        a, b = c * per, ((c + 1) % k) * per
+        W[a, b] = W[b, a] = 0.01
+    from msbm import graph_from_dense
+
+    g = graph_from_dense(W, groups, clusters, k)
+    lam, H, lab, info = solve_and_check(g, k, "fp64")
+    assert metrics.error_rate(lab, clusters, k) == 0.0
+
+
+def test_errors_are_reported(built_lib):
+    from paper_2210_16435_gb300 import binding as B
+    from paper_2210_16435_gb300.solver import FairSC
+
+    g = configs.msbm_n2000_k5_h2(scale=0.1)["graph"]
+    rp, ci, v, gr = graph_tensors(g)
+    bad = gr.clone()
+    bad[0] = 7
+    with pytest.raises(B.SFairSCError) as e:
+        FairSC(rp, ci, v, bad, k=2, h=2)
+    assert e.value.status == -1
+    with pytest.raises(B.SFairSCError) as e:
+        FairSC(rp, ci, v, gr, k=2, h=3)  # group 2 empty
+    assert e.value.status == -4
+    vn = v.clone()
+    vn[3] = float("nan")
+    with pytest.raises(B.SFairSCError) as e:
+        FairSC(rp, ci, vn, gr, k=2, h=2)
+    assert e.value.status == -6
+    cb = ci.clone()
+    cb[0] = g.n + 5
+    with pytest.raises(B.SFairSCError) as e:
+        FairSC(rp, cb, v, gr, k=2, h=2)
+    assert e.value.status == -2
+    with pytest.raises(B.SFairSCError) as e:
+        FairSC(rp, ci, v, gr, k=g.n, h=2)
+    assert e.value.status == -5
