@@ -199,6 +199,10 @@ __global__ void seed_select_kernel(int n, int nb, int bs, const float* __restric
   }
   __syncthreads();
   const int b = found_block;
+  if (b < 0) {  // unreachable when total > 0; keep every index in range regardless
+    if (threadIdx.x == 0) centers[r * k + t] = 0;
+    return;
+  }
   // scan the rows of block b (bs <= 1024 rows)
   const int row = b * bs + threadIdx.x;
   long long q = 0;

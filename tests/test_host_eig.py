@@ -1,0 +1,67 @@
+"""The library's host FP64 symmetric eigensolver (projected matrix of the Krylov method) vs numpy."""
+import ctypes
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+
+SRC = os.path.join(ROOT, "paper_2210_16435_gb300", "csrc", "eig_host.cpp")
+DRIVER = r'''
+#include "internal.h"
+namespace sfairsc {
+void check_cuda(cudaError_t, const char*) {}
+void fail(int, const std::string&) { throw 1; }
+}
+extern "C" void eig(int m, double* A, double* w) { sfairsc::host_symmetric_eig(m, A, w); }
+'''
+
+
+@pytest.fixture(scope="module")
+def eiglib():
+    d = tempfile.mkdtemp()
+    drv = os.path.join(d, "drv.cpp")
+    open(drv, "w").write(DRIVER)
+    so = os.path.join(d, "libeig.so")
+    inc = ["-I" + os.path.join(ROOT, "paper_2210_16435_gb300", "csrc"), "-I/usr/local/cuda/include",
+           "-I" + os.path.join(ROOT, "include")]
+    subprocess.run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", *inc, SRC, drv, "-o", so], check=True)
+    lib = ctypes.CDLL(so)
+    lib.eig.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    return lib
+
+
+@pytest.mark.parametrize("m,seed", [(1, 0), (2, 1), (5, 2), (20, 3), (64, 4), (136, 5)])
+def test_random_symmetric(eiglib, m, seed):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((m, m))
+    A = A + A.T
+    M = np.asfortranarray(A.copy())
+    w = np.empty(m)
+    eiglib.eig(m, M.ctypes.data, w.ctypes.data)
+    ref = np.linalg.eigvalsh(A)
+    np.testing.assert_allclose(w, ref, atol=1e-12 * np.abs(ref).max())
+    V = M
+    np.testing.assert_allclose(V.T @ V, np.eye(m), atol=1e-12)
+    np.testing.assert_allclose(A @ V, V * w, atol=1e-11 * np.abs(ref).max())
+
+
+def test_arrowhead_and_clusters(eiglib):
+    """The thick-restart shape: diagonal Ritz block, coupling row, tridiagonal tail, repeated values."""
+    m, K = 40, 24
+    rng = np.random.default_rng(9)
+    A = np.zeros((m, m))
+    A[np.arange(K), np.arange(K)] = np.sort(np.concatenate([np.zeros(4), np.full(4, 0.3), rng.random(K - 8)]))
+    A[K, :K] = A[:K, K] = rng.standard_normal(K) * 1e-7
+    for i in range(K, m):
+        A[i, i] = rng.random() + 1
+        if i + 1 < m:
+            A[i, i + 1] = A[i + 1, i] = rng.random()
+    M = np.asfortranarray(A.copy())
+    w = np.empty(m)
+    eiglib.eig(m, M.ctypes.data, w.ctypes.data)
+    np.testing.assert_allclose(w, np.linalg.eigvalsh(A), atol=1e-13)
+    np.testing.assert_allclose(A @ M, M * w, atol=1e-12)
