@@ -89,6 +89,7 @@ struct sfairsc_ctx {
   // operator workspace
   OpPlan op;      // main precision
   OpPlan op64;    // FP64 vectors, original values (final residual check)
+  OpPlan proj64;  // FP64 projection P w only
   void* ytil = nullptr;
   double* ytil64 = nullptr;
   double* op_partial = nullptr;
@@ -96,6 +97,7 @@ struct sfairsc_ctx {
   int32_t* cta_rows_orth = nullptr;
   unsigned* barrier = nullptr;
   unsigned* err = nullptr;
+  int* brk_step = nullptr;
 
   // Krylov workspace
   void* V = nullptr;
@@ -312,6 +314,7 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   c->op_partial = c->dalloc<double>((size_t)grid * kMaxGroups * 4);
   c->barrier = c->dalloc<unsigned>(4);
   c->err = c->barrier + 2;
+  c->brk_step = c->dalloc<int>(1);
   check_cuda(cudaMemsetAsync(c->barrier, 0, 4 * sizeof(unsigned), s), "memset");
   OpPlan& o = c->op;
   o.n = n;
@@ -338,6 +341,8 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   c->op64.val_dtype = c->vdt_orig;
   c->op64.dinv = c->dinv64;
   c->op64.ytil = c->ytil64;
+  c->proj64 = c->op64;
+  c->proj64.mode = 1;
 
   // Krylov basis
   c->B = std::max(1, std::min(SFAIRSC_MAX_BLOCK, c->opts.block));
@@ -383,6 +388,7 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   q.cta_rows = c->cta_rows_orth;
   q.barrier = c->barrier;
   q.err = c->err;
+  q.brk_step = c->brk_step;
   check_cuda(cudaMallocHost((void**)&c->Hh, sizeof(double) * c->ldh * m), "pinned allocation");
   check_cuda(cudaMallocHost((void**)&c->Yh, sizeof(double) * m * m), "pinned allocation");
 
@@ -412,7 +418,6 @@ void check_err_word(sfairsc_ctx* c) {
     check_cuda(cudaMemsetAsync(c->barrier, 0, 4 * sizeof(unsigned), c->stream), "memset");
     check_cuda(cudaStreamSynchronize(c->stream), "sync");
     if (e & kErrBarrierTimeout) fail(SFAIRSC_ERR_DEVICE_TIMEOUT, "a grid barrier timed out");
-    if (e & kErrBreakdown) fail(SFAIRSC_ERR_BREAKDOWN, "Krylov block lost rank");
   }
 }
 
@@ -440,83 +445,20 @@ struct Timer {
   }
 };
 
-int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* labels, sfairsc_info* info) {
+// FP64 Ritz vectors X = V[:, 0:mv] Y[:, 0:k] -> project X <- P X (exact F^T H = 0)
+// -> AX = L_n^sigma X with the FP64 operator -> Rayleigh quotients and explicit
+// residual norms ||A x - lambda x|| / ||x||.  V is left untouched.
+double final_check(sfairsc_ctx* c, int mv, const std::vector<double>& T, std::vector<double>& xx) {
   cudaStream_t s = c->stream;
-  const int n = (int)c->n, k = c->k, B = c->B, m = c->m, ldh = c->ldh;
-  const size_t vs = c->vt == VecType::F64 ? 8 : 4;
-  sfairsc_info inf{};
-  inf.sigma = c->sigma;
-  Timer tsolve(s);
-  // start block -> U, orthonormalise into V[:, 0:B]
-  launch_random_block(c->vt, n, c->U, 4, B, c->opts.seed, s);
-  launch_orth(c->orth, c->vt, 0, -1, B, s);
-  check_cuda(cudaMemsetAsync(c->Hd, 0, sizeof(double) * ldh * m, s), "memset");
-  int j0 = 0;
-  int restarts = 0, matvecs = 0;
-  std::vector<double> T((size_t)m * m), theta(m), resid(m);
-  bool converged = false;
-  const double tol = c->opts.tol * c->sigma;
-  for (;;) {
-    for (int j = j0; j < m; j += B) {
-      apply_op(c, false, static_cast<char*>(c->V) + (size_t)j * vs, c->ldv, 1, c->U, 4, 1, B);
-      launch_orth(c->orth, c->vt, j + B, j, B, s);
-      matvecs += B;
-    }
-    check_cuda(cudaMemcpyAsync(c->Hh, c->Hd, sizeof(double) * ldh * m, cudaMemcpyDeviceToHost, s), "d2h");
-    check_err_word(c);  // synchronises
-    // symmetric projected matrix from the upper triangle
-    for (int jj = 0; jj < m; ++jj)
-      for (int ii = 0; ii <= jj; ++ii) {
-        const double v = c->Hh[(size_t)jj * ldh + ii];
-        T[(size_t)jj * m + ii] = v;
-        T[(size_t)ii * m + jj] = v;
-      }
-    host_symmetric_eig(m, T.data(), theta.data());
-    // residual norms ||H[m:m+B, 0:m] y_i||
-    for (int i = 0; i < m; ++i) {
-      double acc = 0.0;
-      for (int r = 0; r < B; ++r) {
-        double sr = 0.0;
-        for (int q = 0; q < m; ++q) sr += c->Hh[(size_t)q * ldh + m + r] * T[(size_t)i * m + q];
-        acc += sr * sr;
-      }
-      resid[i] = std::sqrt(acc);
-    }
-    int nconv = 0;
-    for (int i = 0; i < k; ++i) nconv += resid[i] <= tol;
-    if (nconv == k || restarts >= c->opts.max_restarts) {
-      converged = nconv == k;
-      break;
-    }
-    int K = k + (m - k) / 2;
-    K = std::min(K, m - B);
-    K = std::max(K / B * B, ((k + B - 1) / B) * B);
-    if (K > m - B) K = m - B;
-    for (int i = 0; i < K; ++i)
-      for (int q = 0; q < m; ++q) c->Yh[(size_t)i * m + q] = T[(size_t)i * m + q];
-    check_cuda(cudaMemcpyAsync(c->Yd, c->Yh, sizeof(double) * m * K, cudaMemcpyHostToDevice, s), "h2d");
-    launch_restart(c->vt, n, c->V, c->ldv, m, K, B, c->Yd, s);
-    // new projected matrix: diag(theta) plus the coupling rows of the carried block
-    std::vector<double> Hn((size_t)ldh * m, 0.0);
-    for (int i = 0; i < K; ++i) Hn[(size_t)i * ldh + i] = theta[i];
-    for (int r = 0; r < B; ++r)
-      for (int i = 0; i < K; ++i) {
-        double sr = 0.0;
-        for (int q = 0; q < m; ++q) sr += c->Hh[(size_t)q * ldh + m + r] * T[(size_t)i * m + q];
-        Hn[(size_t)i * ldh + K + r] = sr;
-      }
-    std::memcpy(c->Hh, Hn.data(), sizeof(double) * ldh * m);
-    check_cuda(cudaMemcpyAsync(c->Hd, c->Hh, sizeof(double) * ldh * m, cudaMemcpyHostToDevice, s), "h2d");
-    j0 = K;
-    ++restarts;
-  }
-  // Ritz vectors X = V Y[:, 0:k]
+  const int n = (int)c->n, k = c->k;
   for (int i = 0; i < k; ++i)
-    for (int q = 0; q < m; ++q) c->Yh[(size_t)i * m + q] = T[(size_t)i * m + q];
-  check_cuda(cudaMemcpyAsync(c->Yd, c->Yh, sizeof(double) * m * k, cudaMemcpyHostToDevice, s), "h2d");
-  launch_restart(c->vt, n, c->V, c->ldv, m, k, B, c->Yd, s);
-  launch_to_f64(c->vt, n, c->V, c->ldv, k, c->X64, s);
-  // FP64 Rayleigh quotients and residuals with the FP64 operator
+    for (int q = 0; q < mv; ++q) c->Yh[(size_t)i * mv + q] = T[(size_t)i * mv + q];
+  check_cuda(cudaMemcpyAsync(c->Yd, c->Yh, sizeof(double) * mv * k, cudaMemcpyHostToDevice, s), "h2d");
+  launch_ritz(c->vt, n, c->V, c->ldv, mv, k, c->Yd, c->AX64, s);
+  for (int i = 0; i < k; i += 4) {
+    const int nv = std::min(4, k - i);
+    launch_operator(c->proj64, VecType::F64, c->AX64 + (size_t)i * n, 1, n, c->X64 + (size_t)i * n, 1, n, nv, s);
+  }
   for (int i = 0; i < k; i += 4) {
     const int nv = std::min(4, k - i);
     apply_op(c, true, c->X64 + (size_t)i * n, 1, n, c->AX64 + (size_t)i * n, 1, n, nv);
@@ -525,22 +467,120 @@ int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* label
   std::vector<double> st((size_t)c->stat_blocks * k * 3);
   check_cuda(cudaMemcpyAsync(st.data(), c->stat_partial, st.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "d2h");
   check_err_word(c);
-  std::vector<double> xay(k, 0.0), xx(k, 0.0), ayay(k, 0.0);
+  std::vector<double> xay(k, 0.0);
+  xx.assign(k, 0.0);
   for (int b = 0; b < c->stat_blocks; ++b)
     for (int i = 0; i < k; ++i) {
       xay[i] += st[((size_t)b * k + i) * 3 + 0];
       xx[i] += st[((size_t)b * k + i) * 3 + 1];
-      ayay[i] += st[((size_t)b * k + i) * 3 + 2];
     }
   c->lam_h.assign(k, 0.0);
+  for (int i = 0; i < k; ++i) c->lam_h[i] = xay[i] / xx[i];
+  check_cuda(cudaMemcpyAsync(c->lam_d, c->lam_h.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s), "h2d");
+  launch_column_resid(n, k, c->X64, c->AX64, c->lam_d, c->stat_partial, c->stat_blocks, s);
+  std::vector<double> rp((size_t)c->stat_blocks * k);
+  check_cuda(cudaMemcpyAsync(rp.data(), c->stat_partial, rp.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "d2h");
+  check_cuda(cudaStreamSynchronize(s), "residual");
   double maxres = 0.0;
   for (int i = 0; i < k; ++i) {
-    const double lam = xay[i] / xx[i];
-    c->lam_h[i] = lam;
-    const double r2 = std::max(0.0, (ayay[i] - 2.0 * lam * xay[i] + lam * lam * xx[i]) / xx[i]);
-    maxres = std::max(maxres, std::sqrt(r2) / c->sigma);
+    double r2 = 0.0;
+    for (int b = 0; b < c->stat_blocks; ++b) r2 += rp[(size_t)b * k + i];
+    maxres = std::max(maxres, std::sqrt(r2 / xx[i]) / c->sigma);
   }
-  // order by Rayleigh quotient (they are Ritz-ordered already up to rounding)
+  return maxres;
+}
+
+int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* labels, sfairsc_info* info) {
+  cudaStream_t s = c->stream;
+  const int n = (int)c->n, k = c->k, B = c->B, m = c->m, ldh = c->ldh;
+  const size_t vs = c->vt == VecType::F64 ? 8 : 4;
+  const int kNoBreak = std::numeric_limits<int>::max();
+  sfairsc_info inf{};
+  inf.sigma = c->sigma;
+  Timer tsolve(s);
+  launch_random_block(c->vt, n, c->U, 4, B, c->opts.seed, s);
+  launch_orth(c->orth, c->vt, 0, -1, B, s);
+  check_cuda(cudaMemsetAsync(c->Hd, 0, sizeof(double) * ldh * m, s), "memset");
+  int j0 = 0, restarts = 0, matvecs = 0, since_break = 1 << 20;
+  uint64_t fresh = 0;  // counter for replacement start blocks
+  std::vector<double> T, theta, resid, xx;
+  double maxres = 0.0;
+  bool converged = false;
+  const double tol = c->opts.tol * c->sigma;
+  for (;;) {
+    check_cuda(cudaMemcpyAsync(c->brk_step, &kNoBreak, sizeof(int), cudaMemcpyHostToDevice, s), "h2d");
+    for (int j = j0; j < m; j += B) {
+      apply_op(c, false, static_cast<char*>(c->V) + (size_t)j * vs, c->ldv, 1, c->U, 4, 1, B);
+      launch_orth(c->orth, c->vt, j + B, j, B, s);
+      matvecs += B;
+    }
+    int brk = kNoBreak;
+    check_cuda(cudaMemcpyAsync(c->Hh, c->Hd, sizeof(double) * ldh * m, cudaMemcpyDeviceToHost, s), "d2h");
+    check_cuda(cudaMemcpyAsync(&brk, c->brk_step, sizeof(int), cudaMemcpyDeviceToHost, s), "d2h");
+    check_err_word(c);  // synchronises; a breakdown is handled below, not raised
+    const bool broke = brk != kNoBreak;
+    // basis columns 0..mv-1 are valid: a block that lost rank at step brk is dropped
+    const int mv = broke ? std::max(B, std::min(m, brk + B)) : m;
+    since_break = broke ? 0 : since_break + 1;
+    T.assign((size_t)mv * mv, 0.0);
+    theta.assign(mv, 0.0);
+    resid.assign(mv, 0.0);
+    for (int jj = 0; jj < mv; ++jj)
+      for (int ii = 0; ii <= jj; ++ii) {
+        const double v = c->Hh[(size_t)jj * ldh + ii];
+        T[(size_t)jj * mv + ii] = v;
+        T[(size_t)ii * mv + jj] = v;
+      }
+    host_symmetric_eig(mv, T.data(), theta.data());
+    for (int i = 0; i < mv; ++i) {
+      double acc = 0.0;
+      for (int r = 0; r < B; ++r) {
+        double sr = 0.0;
+        for (int q = 0; q < mv; ++q) sr += c->Hh[(size_t)q * ldh + mv + r] * T[(size_t)i * mv + q];
+        acc += sr * sr;
+      }
+      resid[i] = std::sqrt(acc);
+    }
+    int nconv = 0;
+    for (int i = 0; i < std::min(k, mv); ++i) nconv += resid[i] <= tol;
+    const bool estimate_ok = mv >= k && nconv == k && since_break >= 1;
+    const bool out_of_restarts = restarts >= c->opts.max_restarts;
+    if ((estimate_ok || out_of_restarts) && mv >= k) {
+      maxres = final_check(c, mv, T, xx);
+      if (maxres <= c->opts.tol || out_of_restarts) {
+        converged = maxres <= c->opts.tol;
+        break;
+      }
+      since_break = 0;  // the estimate was optimistic: verify again after another cycle
+    }
+    // thick restart: keep the K smallest Ritz vectors
+    int K = k + (m - k) / 2;
+    K = std::max(K / B * B, ((k + B - 1) / B) * B);
+    K = std::min({K, m - B, mv});
+    for (int i = 0; i < K; ++i)
+      for (int q = 0; q < mv; ++q) c->Yh[(size_t)i * mv + q] = T[(size_t)i * mv + q];
+    check_cuda(cudaMemcpyAsync(c->Yd, c->Yh, sizeof(double) * mv * K, cudaMemcpyHostToDevice, s), "h2d");
+    launch_restart(c->vt, n, c->V, c->ldv, mv, K, B, c->Yd, s);
+    std::vector<double> Hn((size_t)ldh * m, 0.0);
+    for (int i = 0; i < K; ++i) Hn[(size_t)i * ldh + i] = theta[i];
+    if (broke) {
+      // fresh random block orthogonal to the kept Ritz vectors (invariant subspace found)
+      launch_random_block(c->vt, n, c->U, 4, B, c->opts.seed + 0x9E3779B97F4A7C15ull * (++fresh), s);
+      launch_orth(c->orth, c->vt, K, -1, B, s);
+    } else {
+      for (int r = 0; r < B; ++r)
+        for (int i = 0; i < K; ++i) {
+          double sr = 0.0;
+          for (int q = 0; q < mv; ++q) sr += c->Hh[(size_t)q * ldh + mv + r] * T[(size_t)i * mv + q];
+          Hn[(size_t)i * ldh + K + r] = sr;
+        }
+    }
+    std::memcpy(c->Hh, Hn.data(), sizeof(double) * ldh * m);
+    check_cuda(cudaMemcpyAsync(c->Hd, c->Hh, sizeof(double) * ldh * m, cudaMemcpyHostToDevice, s), "h2d");
+    j0 = K;
+    ++restarts;
+  }
+  // order by Rayleigh quotient (Ritz order up to rounding)
   std::vector<int> ord(k);
   for (int i = 0; i < k; ++i) ord[i] = i;
   std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return c->lam_h[a] < c->lam_h[b]; });
@@ -563,8 +603,7 @@ int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* label
   inf.restarts = restarts;
   inf.matvecs = matvecs;
   inf.max_resid = maxres;
-  int status = converged && maxres <= c->opts.tol * 1.0000001 ? SFAIRSC_OK : SFAIRSC_ERR_NOT_CONVERGED;
-  if (converged && maxres > c->opts.tol) status = SFAIRSC_ERR_NOT_CONVERGED;
+  int status = converged ? SFAIRSC_OK : SFAIRSC_ERR_NOT_CONVERGED;
   for (int i = 0; i < k; ++i)
     if (c->lam_h[i] >= c->sigma * (1.0 - 1e-8)) status = SFAIRSC_ERR_SHIFT;
   // unit-norm columns in FP64, then H = D^{-1/2} X with the sign convention

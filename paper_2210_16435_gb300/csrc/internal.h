@@ -42,6 +42,7 @@ struct OpPlan {
   int grid = 0;          // cooperative CTAs
   int threads = 1024;
   int lanes_per_row = 8; // sub-warp width for the SpMV
+  int mode = 0;          // 0: L_n^sigma w, 1: P w
   const int32_t* row_ptr = nullptr;
   const int32_t* col = nullptr;
   const void* val = nullptr;
@@ -92,6 +93,7 @@ struct OrthPlan {
   const int32_t* cta_rows = nullptr;
   unsigned* barrier = nullptr;
   unsigned* err = nullptr;
+  int* brk_step = nullptr;    // smallest step j whose new block lost rank (atomicMin)
 };
 // Orthogonalise the B columns in U against V[:, 0:J] (CGS2), record the
 // coefficients in H[0:J, j:j+B], orthonormalise the block (CholQR), store it
@@ -102,6 +104,12 @@ int orth_max_grid(VecType vt, int B, int threads);
 void launch_restart(VecType vt, int n, void* V, int64_t ldv, int m, int K, int B, const double* Y, cudaStream_t s);
 // Fill V[:, 0:B] with a seeded pseudo-random block.
 void launch_random_block(VecType vt, int n, void* V, int64_t ldv, int B, uint64_t seed, cudaStream_t s);
+// X64 = V[:, 0:m] Y (Y: m x k column-major FP64), X64 n x k column-major FP64; V unchanged.
+void launch_ritz(VecType vt, int n, const void* V, int64_t ldv, int m, int k, const double* Y, double* X64,
+                 cudaStream_t s);
+// partial[b][c] = sum over block b's rows of (AX_c - lam_c X_c)^2.
+void launch_column_resid(int n, int k, const double* X, const double* AX, const double* lam, double* partial,
+                         int nblocks, cudaStream_t s);
 // FP64 copy / conversion of the first k columns of V to X64 (n x k column-major).
 void launch_to_f64(VecType vt, int n, const void* V, int64_t ldv, int k, double* X, cudaStream_t s);
 // Column norms and Rayleigh data: out[c] = <X_c, AX_c>, out[k + c] = <X_c, X_c>, out[2k + c] = ||AX_c - l_c X_c||^2.

@@ -40,6 +40,7 @@ struct OrthArgs {
   const int32_t* __restrict__ cta_rows;
   GridBarrier bar;
   unsigned* err;
+  int* brk_step;
   int J, j;
 };
 
@@ -259,25 +260,33 @@ __global__ void __launch_bounds__(512, 1) orth_kernel(OrthArgs<VT> a) {
     }
   }
   if (!grid_sync(a.bar, a.err)) return;
-  auto cholesky = [&](double* R) {
-    // Gram in gram_s (row-major B x B) = R^T R with R upper triangular.
+  // Gram in gram_s (row-major B x B) = R^T R with R upper triangular.  A
+  // column whose remaining norm vanishes (relative to its input norm) marks a
+  // breakdown: its row of R is zero (recorded in H) and Rdiv keeps a unit
+  // divisor so no value overflows; the host discards that block.
+  __shared__ double Rdiv1[16], Rdiv2[16];
+  auto cholesky = [&](double* R, double* Rdiv) {
     if (threadIdx.x == 0) {
-      for (int i = 0; i < B * B; ++i) R[i] = 0.0;
+      for (int i = 0; i < B * B; ++i) R[i] = Rdiv[i] = 0.0;
       for (int c = 0; c < B; ++c) {
         double dsum = gram_s[c * B + c];
         for (int q = 0; q < c; ++q) dsum -= R[q * B + c] * R[q * B + c];
         const double ref = unorm[c] > 0.0 ? unorm[c] : gram_s[c * B + c];
-        const double floor_rel = sizeof(VT) == 8 ? 1e-26 : 1e-12;
+        const double floor_rel = sizeof(VT) == 8 ? 1e-24 : 1e-10;
         if (!(dsum > floor_rel * ref) || !(dsum > 0.0)) {
           brk = 1;
-          dsum = 1.0;
+          R[c * B + c] = dsum > 0.0 ? sqrt(dsum) : 0.0;
+          Rdiv[c * B + c] = 1.0;
+          continue;
         }
         const double rc = sqrt(dsum);
         R[c * B + c] = rc;
+        Rdiv[c * B + c] = rc;
         for (int q = c + 1; q < B; ++q) {
           double s = gram_s[c * B + q];
           for (int p = 0; p < c; ++p) s -= R[p * B + c] * R[p * B + q];
           R[c * B + q] = s / rc;
+          Rdiv[c * B + q] = s / rc;
         }
       }
     }
@@ -289,7 +298,7 @@ __global__ void __launch_bounds__(512, 1) orth_kernel(OrthArgs<VT> a) {
     gram_s[threadIdx.x] = s;
   }
   __syncthreads();
-  cholesky(R1);
+  cholesky(R1, Rdiv1);
 
   // Row-wise triangular solve x R = u (R upper): x_v = (u_v - sum_{q<v} x_q R_qv) / R_vv.
   auto tri = [&](const double* R, VT (&u)[B]) {
@@ -309,7 +318,7 @@ __global__ void __launch_bounds__(512, 1) orth_kernel(OrthArgs<VT> a) {
     for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
       VT u[B];
       load_u<VT, B>(U, r, u);
-      tri(R1, u);
+      tri(Rdiv1, u);
 #pragma unroll
       for (int v = 0; v < B; ++v) U[(size_t)r * 4 + v] = u[v];
 #pragma unroll
@@ -338,9 +347,12 @@ __global__ void __launch_bounds__(512, 1) orth_kernel(OrthArgs<VT> a) {
     }
     if (threadIdx.x < B) unorm[threadIdx.x] = 0.0;
     __syncthreads();
-    cholesky(R2);
+    cholesky(R2, Rdiv2);
   } else {
-    if (threadIdx.x == 0) R2[0] = 1.0;
+    if (threadIdx.x == 0) {
+      R2[0] = 1.0;
+      Rdiv2[0] = 1.0;
+    }
     __syncthreads();
   }
 
@@ -348,13 +360,16 @@ __global__ void __launch_bounds__(512, 1) orth_kernel(OrthArgs<VT> a) {
   for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
     VT u[B];
     load_u<VT, B>(U, r, u);
-    if (B > 1) tri(R2, u);
-    else u[0] = u[0] / (VT)R1[0];
+    if (B > 1) tri(Rdiv2, u);
+    else u[0] = u[0] / (VT)Rdiv1[0];
 #pragma unroll
     for (int v = 0; v < B; ++v) a.V[(size_t)r * a.ldv + J + v] = u[v];
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    if (brk) atomicOr(a.err, kErrBreakdown);
+    if (brk) {
+      atomicOr(a.err, kErrBreakdown);
+      atomicMin(a.brk_step, a.j);
+    }
     if (a.j >= 0) {
       for (int q = 0; q < B; ++q)
         for (int v = 0; v < B; ++v) {
@@ -388,6 +403,7 @@ static void orth_launch_t(const OrthPlan& p, int J, int j, cudaStream_t s) {
   a.cta_rows = p.cta_rows;
   a.bar = GridBarrier{p.barrier, p.barrier + 1};
   a.err = p.err;
+  a.brk_step = p.brk_step;
   a.J = J;
   a.j = j;
   const size_t smem = orth_smem(p.threads, B, MAXG, sizeof(VT));
@@ -500,6 +516,90 @@ void launch_restart(VecType vt, int n, void* V, int64_t ldv, int m, int K, int B
     restart_kernel<float><<<grid, 1024, smem, s>>>(n, (float*)V, ldv, m, K, B, Y);
   }
   check_cuda(cudaGetLastError(), "restart launch");
+}
+
+// X64[r + c n] = sum_q V[r, q] Y[q, c]: a 32-row tile of V in shared memory,
+// warp per row, lanes over output columns.  V is not modified.
+template <typename VT>
+__global__ void __launch_bounds__(1024) ritz_kernel(int n, const VT* V, int64_t ldv, int m, int k,
+                                                   const double* __restrict__ Y, double* X) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  VT* Vs = reinterpret_cast<VT*>(sm);  // 32 x m
+  VT* Ys = Vs + 32 * m;                // m x 64
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int rbase = blockIdx.x * 32;
+  const int rows = min(32, n - rbase);
+  for (int i = threadIdx.x; i < rows * m; i += blockDim.x) {
+    const int rr = i / m, c = i % m;
+    Vs[rr * m + c] = V[(size_t)(rbase + rr) * ldv + c];
+  }
+  for (int k0 = 0; k0 < k; k0 += 64) {
+    const int kc = min(64, k - k0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < m * 64; i += blockDim.x) {
+      const int c = i / 64, kk = i % 64;
+      Ys[i] = kk < kc ? (VT)Y[(size_t)c + (size_t)(k0 + kk) * m] : VT(0);
+    }
+    __syncthreads();
+    if (warp < rows) {
+      VT acc0 = VT(0), acc1 = VT(0);
+      const VT* vr = Vs + warp * m;
+      for (int c = 0; c < m; ++c) {
+        const VT x = vr[c];
+        acc0 = fma(x, Ys[c * 64 + lane], acc0);
+        acc1 = fma(x, Ys[c * 64 + 32 + lane], acc1);
+      }
+      const int r = rbase + warp;
+      if (lane < kc) X[(size_t)r + (size_t)(k0 + lane) * n] = (double)acc0;
+      if (32 + lane < kc) X[(size_t)r + (size_t)(k0 + 32 + lane) * n] = (double)acc1;
+    }
+  }
+}
+
+void launch_ritz(VecType vt, int n, const void* V, int64_t ldv, int m, int k, const double* Y, double* X64,
+                 cudaStream_t s) {
+  const int grid = (n + 31) / 32;
+  if (vt == VecType::F64) {
+    const size_t smem = sizeof(double) * (32 * (size_t)m + (size_t)m * 64);
+    check_cuda(cudaFuncSetAttribute(ritz_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "ritz smem");
+    ritz_kernel<double><<<grid, 1024, smem, s>>>(n, (const double*)V, ldv, m, k, Y, X64);
+  } else {
+    const size_t smem = sizeof(float) * (32 * (size_t)m + (size_t)m * 64);
+    check_cuda(cudaFuncSetAttribute(ritz_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "ritz smem");
+    ritz_kernel<float><<<grid, 1024, smem, s>>>(n, (const float*)V, ldv, m, k, Y, X64);
+  }
+  check_cuda(cudaGetLastError(), "ritz launch");
+}
+
+__global__ void column_resid_kernel(int n, int k, const double* __restrict__ X, const double* __restrict__ AX,
+                                    const double* __restrict__ lam, double* partial) {
+  __shared__ double red[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int per = (n + gridDim.x - 1) / gridDim.x;
+  const int lo = blockIdx.x * per, hi = min(n, lo + per);
+  for (int c = 0; c < k; ++c) {
+    double s = 0.0;
+    const double l = lam[c];
+    for (int r = lo + threadIdx.x; r < hi; r += blockDim.x) {
+      const double t = AX[(size_t)c * n + r] - l * X[(size_t)c * n + r];
+      s = fma(t, t, s);
+    }
+    s = warp_allsum(s);
+    if (lane == 0) red[warp] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < nw; ++w) t += red[w];
+      partial[(size_t)blockIdx.x * k + c] = t;
+    }
+    __syncthreads();
+  }
+}
+
+void launch_column_resid(int n, int k, const double* X, const double* AX, const double* lam, double* partial,
+                         int nblocks, cudaStream_t s) {
+  column_resid_kernel<<<nblocks, 256, 0, s>>>(n, k, X, AX, lam, partial);
+  check_cuda(cudaGetLastError(), "column resid launch");
 }
 
 // ---------------------------------------------------------------- start block

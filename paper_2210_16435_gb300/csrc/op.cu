@@ -26,6 +26,7 @@ namespace sfairsc {
 template <typename VT, typename MT>
 struct OpArgs {
   int n, h, normalized, lanes;
+  int mode;  // 0: out = L_n^sigma w;  1: out = P w (projection only)
   const int32_t* __restrict__ row_ptr;
   const int32_t* __restrict__ col;
   const MT* __restrict__ val;
@@ -210,6 +211,15 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
     }
     __syncthreads();
   }
+  if (a.mode == 1) {  // P w only
+    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+      const int g = a.lab[r];
+      const VT sc = scale(r);
+#pragma unroll
+      for (int v = 0; v < B; ++v) a.out[r * a.ors + v * a.ocs] = a.w[r * a.wrs + v * a.wcs] - sc * (VT)coefA[g * B + v];
+    }
+    return;
+  }
   for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
     const int g = a.lab[r];
     const VT sc = scale(r);
@@ -337,6 +347,7 @@ static void launch_t(const OpPlan& p, const void* w, int64_t wrs, int64_t wcs, v
   a.h = p.h;
   a.normalized = p.normalized;
   a.lanes = p.lanes_per_row;
+  a.mode = p.mode;
   a.row_ptr = p.row_ptr;
   a.col = p.col;
   a.val = static_cast<const MT*>(p.val);
