@@ -1,0 +1,405 @@
+#!/usr/bin/env python
+"""Benchmark: k smallest eigenpairs of the s-FairSC operator + embedding + k-means
+(Algorithm 3 end to end) on a synthetic m-SBM workload, one solve per step.
+
+Default workload: msbm_n1m_k50_h10 (n = 1,000,000, k = 50 Dirichlet(5)-sized
+clusters, h = 10 Zipf(1) groups, mean degree 32 split 50/25/15/10, BF16 0/1
+weights, seed 2), mixed precision, Krylov block 4, residual tol 1e-6 * sigma.
+A step = sfairsc_create (setup) + sfairsc_solve (eigensolve, embedding,
+k-means) on device-resident inputs.  value = seconds per solve (job level).
+
+python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun each rank solves its own replica (weak scaling, no data-path
+collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fused fair-operator HBM GB/s; k-eigpair solve s, mixed/batched vs plain FP64 @1e-6"
+VDT_BYTES = {"f64": 8, "f32": 4, "bf16": 2}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="msbm_n1m_k50_h10")
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--block", type=int, default=4)
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64 / operator / e2e / CPU side measurements")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def load_workload(name):
+    from msbm import configs
+
+    c = configs.BUILDERS[name]()
+    if "graphs" in c:
+        raise SystemExit("batched workload: use the batched bench entry")
+    return c
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- roofline arithmetic
+def operator_bytes(n, nnz, s_v, s_x, b):
+    """Algorithmic bytes of one fused operator launch on b vectors.
+
+    row_ptr 4(n+1) + col 4 nnz + values s_v nnz (read once), the b input and
+    b output vectors (s_x each), the uint8 labels and D^{-1/2} (s_x) per row.
+    """
+    return 4 * (n + 1) + nnz * (4 + s_v) + n * (2 * b * s_x + 1 + s_x)
+
+
+def orth_bytes(n, sum_cols, launches, s_x, b):
+    """Algorithmic bytes of the CGS2 launches: V[:, 0:J] is read three times per
+    launch (coefficients, first update fused with the second coefficients,
+    second update), the new block is read once and written once."""
+    return 3 * n * s_x * sum_cols + launches * 2 * n * b * s_x
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- oracle on the host cores
+def oracle_estimate(g, k, h, budget_s=12.0, step_model=None):
+    """Seconds per solve of the CPU oracle, from a bounded timed sample.
+
+    The oracle (FP64 NumPy/SciPy, oracle/) is timed on the full graph: its
+    setup, operator applications (eq. asigma via Sec. 3.4) and full
+    reorthogonalisation at the average basis width; the step count is the
+    oracle's own thick-restart Lanczos count to tol 1e-6 on the same m-SBM
+    shape at n = 50,000 (step_model).  Returns (seconds per solve, sample text).
+    """
+    import numpy as np
+
+    from oracle.sfairsc import operator_from_graph
+
+    t0 = time.perf_counter()
+    op = operator_from_graph(g)
+    t_setup = time.perf_counter() - t0
+    m = max(2 * k, 20)
+    jbar = (k + (m - k) // 2 + m) // 2
+    rng = np.random.default_rng(0)
+    w = rng.standard_normal(g.n)
+    reps = 0
+    t0 = time.perf_counter()
+    while reps < 3 or (time.perf_counter() - t0 < budget_s / 3 and reps < 50):
+        op.apply(w)
+        reps += 1
+    t_op = (time.perf_counter() - t0) / reps
+    V = rng.standard_normal((g.n, jbar))
+    reps2 = 0
+    t0 = time.perf_counter()
+    while reps2 < 2 or (time.perf_counter() - t0 < budget_s / 3 and reps2 < 50):
+        for _ in range(2):
+            c = V.T @ w
+            w = w - V @ c
+        reps2 += 1
+    t_re = (time.perf_counter() - t0) / reps2
+    Y = rng.standard_normal((jbar, k))
+    t0 = time.perf_counter()
+    V @ Y
+    t_restart = (time.perf_counter() - t0) * (m / jbar) * ((k + (m - k) // 2) / k)
+    matvecs, restarts = step_model
+    est = t_setup + matvecs * (t_op + t_re) + restarts * t_restart
+    sample = (f"oracle on the full graph: setup {t_setup:.2f}s, {reps} operator applications "
+              f"({t_op:.3f}s each), {reps2} CGS2 sweeps at width {jbar} ({t_re:.3f}s each), one restart "
+              f"product; scaled by the oracle's own Lanczos counts on the n=50,000 instance of this shape "
+              f"({matvecs} matvecs, {restarts} restarts)")
+    return est, sample
+
+
+def oracle_step_model(name, k):
+    """The oracle's matvec and restart counts to tol 1e-6 on the n = 50,000 instance of the workload's shape."""
+    from msbm import configs
+    from oracle.lanczos import thick_restart_lanczos
+    from oracle.sfairsc import operator_from_graph
+
+    c = configs.BUILDERS[name](scale=0.05) if name != "msbm_n2000_k5_h2" else configs.BUILDERS[name]()
+    op = operator_from_graph(c["graph"])
+    _, _, info = thick_restart_lanczos(op.apply, op.n, k, tol=1e-6, anorm=op.sigma, seed=0)
+    return info["matvecs"], info["restarts"]
+
+
+def host_threads():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+# ---------------------------------------------------------------- arms
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    c = load_workload(args.workload)
+    g, k, h = c["graph"], c["k"], c["h"]
+    model = oracle_step_model(args.workload, k)
+    for _ in range(args.warmup):
+        oracle_estimate(g, k, h, budget_s=3.0, step_model=model)
+    vals = []
+    t0 = time.perf_counter()
+    sample = ""
+    for _ in range(args.steps):
+        v, sample = oracle_estimate(g, k, h, budget_s=6.0, step_model=model)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    value = statistics.median(vals)
+    cores = host_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "s/solve", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall * 1e3 / max(args.steps, 1),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n": g.n, "nnz": g.nnz, "k": k, "h": h, "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": "s/solve", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "s/solve", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2210_16435_gb300 import buildlib
+
+    buildlib.build()
+    from paper_2210_16435_gb300 import binding as B
+    from paper_2210_16435_gb300.solver import FairSC
+
+    c = load_workload(args.workload)
+    g, k, h = c["graph"], c["k"], c["h"]
+    vdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[c["value_dtype"]]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    T = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    rp, ci, v, gr = T(g.row_ptr, torch.int32), T(g.col_idx, torch.int32), T(g.values, vdt), T(g.groups, torch.int32)
+    kw = dict(k=k, h=h, prec=args.prec, block=args.block, profile=1)
+
+    def step():
+        s = FairSC(rp, ci, v, gr, **kw)
+        lam, H, lab, info = s.solve()
+        s.close()
+        return info
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        infos.append(step())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ms / 1e3 / world  # seconds per solve at the job level (world replicas per step)
+
+    s_x = 8 if args.prec == "fp64" else 4
+    s_v = VDT_BYTES[c["value_dtype"]] if not (args.prec == "mixed" and c["value_dtype"] == "f64") else 4
+    inf = infos[-1]
+    b = inf["block"]
+    op_avg_ms = sum(i["ms_operator"] for i in infos) / max(1, sum(i["n_operator"] for i in infos))
+    orth_avg_ms = sum(i["ms_orth"] for i in infos) / max(1, sum(i["n_orth"] for i in infos))
+    op_bytes = operator_bytes(g.n, g.nnz, s_v, s_x, b)
+    orth_b = orth_bytes(g.n, inf["orth_cols"], inf["n_orth"], s_x, b) / max(1, inf["n_orth"])
+    peak, peak_kind = measured_peaks()
+    op_gbs = op_bytes / (op_avg_ms * 1e6)
+    orth_gbs = orth_b / (orth_avg_ms * 1e6)
+    t_op = sum(i["ms_operator"] for i in infos)
+    t_orth = sum(i["ms_orth"] for i in infos)
+    if t_orth >= t_op:
+        roof = {"kernel": "orth_kernel (CGS2 + CholQR)", "bound": "hbm", "achieved": orth_gbs, "peak": peak,
+                "unit": "GB/s", "frac": orth_gbs / peak, "traffic": None,
+                "bytes_per_launch": orth_b, "ms_per_launch": orth_avg_ms}
+    else:
+        roof = {"kernel": "fused_operator_kernel", "bound": "hbm", "achieved": op_gbs, "peak": peak, "unit": "GB/s",
+                "frac": op_gbs / peak, "traffic": None, "bytes_per_launch": op_bytes, "ms_per_launch": op_avg_ms}
+    roof["peak_kind"] = f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind
+    launches = sum(i["n_launches"] for i in infos) + 5 * args.steps  # + create: validate, degrees, sigma, partition, (convert)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "s/solve", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.prec == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n": g.n, "nnz": g.nnz, "k": k, "h": h, "prec": args.prec,
+                   "block": b, "basis": inf["basis"], "tol": 1e-6, "values": c["value_dtype"],
+                   "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (CSR 192 MB, basis 400+ MB)"},
+        "roofline": roof, "clocks": clk, "gpu_launches": launches,
+        "solve": {"restarts": inf["restarts"], "matvecs": inf["matvecs"], "max_resid": inf["max_resid"],
+                  "fairness_err": inf["fairness_err"], "dorth_err": inf["dorth_err"],
+                  "ms_solve": inf["ms_solve"], "ms_kmeans": inf["ms_kmeans"], "kmeans_iters": inf["kmeans_iters"],
+                  "ms_operator_total": inf["ms_operator"], "ms_orth_total": inf["ms_orth"]},
+        "operator_in_solve": {"achieved_gbs": op_gbs, "frac": op_gbs / peak, "ms_per_launch": op_avg_ms,
+                              "bytes_per_launch": op_bytes},
+    }
+    if rank == 0 and not args.no_extras:
+        # standalone fused operator on the workload (the metric's operator GB/s), b = 1 and 4
+        s = FairSC(rp, ci, v, gr, k=k, h=h, prec=args.prec, block=args.block)
+        opx = {}
+        for nv in (1, 4):
+            Wc = torch.randn(nv, g.n, device=dev, dtype=s.vec_dtype)
+            O = torch.empty_like(Wc)
+            for _ in range(5):
+                B.sfairsc_apply_operator(s.ctx, Wc.data_ptr(), O.data_ptr(), nv)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a0.record(stream)
+            reps = 50
+            for _ in range(reps):
+                B.sfairsc_apply_operator(s.ctx, Wc.data_ptr(), O.data_ptr(), nv)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            oms = a0.elapsed_time(a1) / reps
+            ob = operator_bytes(g.n, g.nnz, s_v, s_x, nv)
+            opx[f"nvec{nv}"] = {"us": oms * 1e3, "achieved_gbs": ob / (oms * 1e6), "frac": ob / (oms * 1e6) / peak,
+                                "bytes": ob}
+        s.close()
+        line["operator"] = opx
+        # plain FP64 GPU path (block 1) on the same graph, once
+        t0 = time.perf_counter()
+        s = FairSC(rp, ci, v, gr, k=k, h=h, prec="fp64", block=1)
+        _, _, _, i64 = s.solve()
+        torch.cuda.synchronize()
+        line["fp64_block1_solve_s"] = time.perf_counter() - t0
+        line["fp64_block1_info"] = {"restarts": i64["restarts"], "matvecs": i64["matvecs"],
+                                    "max_resid": i64["max_resid"]}
+        s.close()
+        # end to end through the C ABI with host buffers: copies inside the timed region
+        hp = [torch.as_tensor(np.ascontiguousarray(a), dtype=dt).pin_memory()
+              for a, dt in ((g.row_ptr, torch.int32), (g.col_idx, torch.int32), (g.values, vdt),
+                            (g.groups, torch.int32))]
+        ne = max(1, min(3, args.steps))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ne):
+            s = FairSC(*hp, k=k, h=h, prec=args.prec, block=args.block)
+            lam, H, lab, _ = s.solve(on_host=True)
+            s.close()
+        torch.cuda.synchronize()
+        e2e = (time.perf_counter() - t0) / ne
+        h2d = 4 * (g.n + 1) + 4 * g.nnz + VDT_BYTES[c["value_dtype"]] * g.nnz + 4 * g.n
+        d2h = 8 * k + 8 * g.n * k + 4 * g.n
+        line["e2e"] = {"value": e2e, "unit": "s/solve", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        # the CPU oracle on the host cores (bounded sample, scaled to seconds per solve)
+        if world == 1:
+            model = oracle_step_model(args.workload, k)
+            est, sample = oracle_estimate(g, k, h, budget_s=15.0, step_model=model)
+            line["cpu_baseline"] = {"value": est, "unit": "s/solve", "cores": host_threads(), "kind": "oracle",
+                                    "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

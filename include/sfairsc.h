@@ -91,7 +91,8 @@ typedef struct {
   int32_t kmeans_n_init;   /* replicates, best inertia wins; default 1 */
   int32_t kmeans_max_iter; /* Lloyd assignments per replicate; default 100 */
   int32_t validate;        /* 0: none, 1: structure checks (default), 2: also symmetry (sorted columns) */
-  int32_t reserved[9];
+  int32_t profile;         /* 1: time the operator and orthogonalisation kernels with CUDA events (info.ms_*) */
+  int32_t reserved[8];
 } sfairsc_opts;
 
 typedef struct {
@@ -105,7 +106,14 @@ typedef struct {
   double dorth_err;        /* max |H^T D H - I| over entries */
   double kmeans_inertia;   /* sum of squared distances of the winning replicate */
   float ms_setup, ms_solve, ms_kmeans, ms_total;
-  int32_t reserved[8];
+  float ms_operator;       /* with opts.profile: summed device time of the fused operator launches */
+  float ms_orth;           /* with opts.profile: summed device time of the CGS2 orthogonalisation launches */
+  int32_t n_operator;      /* fused operator launches in the solve (main precision) */
+  int32_t n_orth;          /* orthogonalisation launches in the solve */
+  int32_t n_launches;      /* all kernels this call launched */
+  int32_t orth_cols;       /* sum over orthogonalisation launches of the basis columns J swept */
+  int32_t basis;           /* Krylov basis size m in use */
+  int32_t block;           /* Krylov block size b in use */
 } sfairsc_info;
 
 typedef struct sfairsc_ctx sfairsc_ctx;

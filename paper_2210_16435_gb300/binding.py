@@ -27,7 +27,8 @@ class Opts(ctypes.Structure):
         ("sigma", ctypes.c_double), ("tol", ctypes.c_double), ("max_restarts", ctypes.c_int32),
         ("basis", ctypes.c_int32), ("prec", ctypes.c_int32), ("block", ctypes.c_int32),
         ("seed", ctypes.c_uint64), ("kmeans_seed", ctypes.c_uint64), ("kmeans_n_init", ctypes.c_int32),
-        ("kmeans_max_iter", ctypes.c_int32), ("validate", ctypes.c_int32), ("reserved", ctypes.c_int32 * 9),
+        ("kmeans_max_iter", ctypes.c_int32), ("validate", ctypes.c_int32), ("profile", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 8),
     ]
 
 
@@ -37,11 +38,13 @@ class Info(ctypes.Structure):
         ("kmeans_iters", ctypes.c_int32), ("sigma", ctypes.c_double), ("max_resid", ctypes.c_double),
         ("fairness_err", ctypes.c_double), ("dorth_err", ctypes.c_double), ("kmeans_inertia", ctypes.c_double),
         ("ms_setup", ctypes.c_float), ("ms_solve", ctypes.c_float), ("ms_kmeans", ctypes.c_float),
-        ("ms_total", ctypes.c_float), ("reserved", ctypes.c_int32 * 8),
+        ("ms_total", ctypes.c_float), ("ms_operator", ctypes.c_float), ("ms_orth", ctypes.c_float),
+        ("n_operator", ctypes.c_int32), ("n_orth", ctypes.c_int32), ("n_launches", ctypes.c_int32),
+        ("orth_cols", ctypes.c_int32), ("basis", ctypes.c_int32), ("block", ctypes.c_int32),
     ]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class SFairSCError(RuntimeError):
@@ -154,7 +157,7 @@ def sfairsc_backward(ctx, grad_lambda, grad_values, bandwidth=0.0, want_bandwidt
 
 
 def make_opts(prec="mixed", block=1, tol=1e-6, basis=0, max_restarts=200, sigma=None, seed=1, kmeans_seed=0,
-              kmeans_n_init=1, kmeans_max_iter=100, validate=1) -> Opts:
+              kmeans_n_init=1, kmeans_max_iter=100, validate=1, profile=0) -> Opts:
     o = sfairsc_opts_default()
     o.prec = SFAIRSC_PREC_FP64 if prec == "fp64" else SFAIRSC_PREC_MIXED
     o.block = int(block)
@@ -167,4 +170,5 @@ def make_opts(prec="mixed", block=1, tol=1e-6, basis=0, max_restarts=200, sigma=
     o.kmeans_n_init = int(kmeans_n_init)
     o.kmeans_max_iter = int(kmeans_max_iter)
     o.validate = int(validate)
+    o.profile = int(profile)
     return o

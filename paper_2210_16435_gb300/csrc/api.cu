@@ -102,6 +102,7 @@ struct sfairsc_ctx {
   // Krylov workspace
   void* V = nullptr;
   void* U = nullptr;
+  void* Q = nullptr;
   double* Hd = nullptr;
   double* Yd = nullptr;
   double* orth_partial = nullptr;
@@ -126,6 +127,20 @@ struct sfairsc_ctx {
   int32_t* labels_d = nullptr;
   std::vector<double> lam_h;
   bool solved = false;
+  // live kernel timing (opts.profile) and launch counting
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_op, ev_orth;
+  int n_launches = 0;
+  cudaEvent_t take_event() {
+    if (ev_pool.empty()) {
+      cudaEvent_t e;
+      check_cuda(cudaEventCreate(&e), "event create");
+      return e;
+    }
+    cudaEvent_t e = ev_pool.back();
+    ev_pool.pop_back();
+    return e;
+  }
 
   template <typename T>
   T* dalloc(size_t count) {
@@ -135,6 +150,9 @@ struct sfairsc_ctx {
     return static_cast<T*>(p);
   }
   ~sfairsc_ctx() {
+    for (auto& pr : ev_op) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+    for (auto& pr : ev_orth) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     for (void* p : owned) cudaFree(p);
     if (Hh) cudaFreeHost(Hh);
     if (Yh) cudaFreeHost(Yh);
@@ -361,7 +379,9 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   c->ldh = m + c->B;
   c->V = c->dalloc<unsigned char>((size_t)n * c->ldv * vs);
   c->U = c->dalloc<unsigned char>((size_t)n * 4 * vs);
+  c->Q = c->dalloc<unsigned char>((size_t)n * 4 * vs);
   check_cuda(cudaMemsetAsync(c->U, 0, (size_t)n * 4 * vs, s), "memset");
+  check_cuda(cudaMemsetAsync(c->Q, 0, (size_t)n * 4 * vs, s), "memset");
   c->Hd = c->dalloc<double>((size_t)c->ldh * m);
   c->Yd = c->dalloc<double>((size_t)m * m);
   const int ogmax = orth_max_grid(c->vt, c->B, 512);
@@ -381,6 +401,7 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   q.ldv = c->ldv;
   q.V = c->V;
   q.U = c->U;
+  q.Q = c->Q;
   q.H = c->Hd;
   q.ldh = c->ldh;
   q.partial = c->orth_partial;
@@ -424,7 +445,49 @@ void check_err_word(sfairsc_ctx* c) {
 void apply_op(sfairsc_ctx* c, bool fp64, const void* w, int64_t wrs, int64_t wcs, void* out, int64_t ors, int64_t ocs,
               int nvec) {
   const OpPlan& p = fp64 ? c->op64 : c->op;
+  const bool timed = c->opts.profile && !fp64;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (timed) {
+    a = c->take_event();
+    b = c->take_event();
+    check_cuda(cudaEventRecord(a, c->stream), "event record");
+  }
   launch_operator(p, fp64 ? VecType::F64 : c->vt, w, wrs, wcs, out, ors, ocs, nvec, c->stream);
+  c->n_launches += (nvec + 3) / 4 + ((nvec & 3) == 3 ? 1 : 0);
+  if (timed) {
+    check_cuda(cudaEventRecord(b, c->stream), "event record");
+    c->ev_op.emplace_back(a, b);
+  }
+}
+
+void orth(sfairsc_ctx* c, int J, int j) {
+  const bool timed = c->opts.profile != 0;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (timed) {
+    a = c->take_event();
+    b = c->take_event();
+    check_cuda(cudaEventRecord(a, c->stream), "event record");
+  }
+  launch_orth(c->orth, c->vt, J, j, c->B, c->stream);
+  c->n_launches += 1;
+  if (timed) {
+    check_cuda(cudaEventRecord(b, c->stream), "event record");
+    c->ev_orth.emplace_back(a, b);
+  }
+}
+
+// Sum and recycle the recorded event pairs (the stream must be synchronised).
+float drain_events(sfairsc_ctx* c, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>& v) {
+  float tot = 0.f;
+  for (auto& pr : v) {
+    float ms = 0.f;
+    check_cuda(cudaEventElapsedTime(&ms, pr.first, pr.second), "event time");
+    tot += ms;
+    c->ev_pool.push_back(pr.first);
+    c->ev_pool.push_back(pr.second);
+  }
+  v.clear();
+  return tot;
 }
 
 struct Timer {
@@ -455,6 +518,7 @@ double final_check(sfairsc_ctx* c, int mv, const std::vector<double>& T, std::ve
     for (int q = 0; q < mv; ++q) c->Yh[(size_t)i * mv + q] = T[(size_t)i * mv + q];
   check_cuda(cudaMemcpyAsync(c->Yd, c->Yh, sizeof(double) * mv * k, cudaMemcpyHostToDevice, s), "h2d");
   launch_ritz(c->vt, n, c->V, c->ldv, mv, k, c->Yd, c->AX64, s);
+  c->n_launches += 3 + (k + 3) / 4;
   for (int i = 0; i < k; i += 4) {
     const int nv = std::min(4, k - i);
     launch_operator(c->proj64, VecType::F64, c->AX64 + (size_t)i * n, 1, n, c->X64 + (size_t)i * n, 1, n, nv, s);
@@ -498,8 +562,12 @@ int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* label
   sfairsc_info inf{};
   inf.sigma = c->sigma;
   Timer tsolve(s);
+  c->n_launches = 0;
+  int n_op = 0, n_orth = 0, orth_cols = 0;
+  float ms_op = 0.f, ms_orth = 0.f;
   launch_random_block(c->vt, n, c->U, 4, B, c->opts.seed, s);
-  launch_orth(c->orth, c->vt, 0, -1, B, s);
+  orth(c, 0, -1);
+  c->n_launches += 1;
   check_cuda(cudaMemsetAsync(c->Hd, 0, sizeof(double) * ldh * m, s), "memset");
   int j0 = 0, restarts = 0, matvecs = 0, since_break = 1 << 20;
   uint64_t fresh = 0;  // counter for replacement start blocks
@@ -510,14 +578,21 @@ int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* label
   for (;;) {
     check_cuda(cudaMemcpyAsync(c->brk_step, &kNoBreak, sizeof(int), cudaMemcpyHostToDevice, s), "h2d");
     for (int j = j0; j < m; j += B) {
-      apply_op(c, false, static_cast<char*>(c->V) + (size_t)j * vs, c->ldv, 1, c->U, 4, 1, B);
-      launch_orth(c->orth, c->vt, j + B, j, B, s);
+      apply_op(c, false, c->Q, 4, 1, c->U, 4, 1, B);  // Q holds V[:, j:j+B]
+      orth(c, j + B, j);
+      orth_cols += j + B;
       matvecs += B;
+      ++n_op;
+      ++n_orth;
     }
     int brk = kNoBreak;
     check_cuda(cudaMemcpyAsync(c->Hh, c->Hd, sizeof(double) * ldh * m, cudaMemcpyDeviceToHost, s), "d2h");
     check_cuda(cudaMemcpyAsync(&brk, c->brk_step, sizeof(int), cudaMemcpyDeviceToHost, s), "d2h");
     check_err_word(c);  // synchronises; a breakdown is handled below, not raised
+    if (c->opts.profile) {
+      ms_op += drain_events(c, c->ev_op);
+      ms_orth += drain_events(c, c->ev_orth);
+    }
     const bool broke = brk != kNoBreak;
     // basis columns 0..mv-1 are valid: a block that lost rank at step brk is dropped
     const int mv = broke ? std::max(B, std::min(m, brk + B)) : m;
@@ -560,13 +635,17 @@ int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* label
     for (int i = 0; i < K; ++i)
       for (int q = 0; q < mv; ++q) c->Yh[(size_t)i * mv + q] = T[(size_t)i * mv + q];
     check_cuda(cudaMemcpyAsync(c->Yd, c->Yh, sizeof(double) * mv * K, cudaMemcpyHostToDevice, s), "h2d");
-    launch_restart(c->vt, n, c->V, c->ldv, mv, K, B, c->Yd, s);
+    launch_restart(c->vt, n, c->V, c->ldv, mv, K, B, c->Yd, c->Q, s);
+    c->n_launches += 1;
     std::vector<double> Hn((size_t)ldh * m, 0.0);
     for (int i = 0; i < K; ++i) Hn[(size_t)i * ldh + i] = theta[i];
     if (broke) {
       // fresh random block orthogonal to the kept Ritz vectors (invariant subspace found)
       launch_random_block(c->vt, n, c->U, 4, B, c->opts.seed + 0x9E3779B97F4A7C15ull * (++fresh), s);
-      launch_orth(c->orth, c->vt, K, -1, B, s);
+      orth(c, K, -1);
+      c->n_launches += 1;
+      ++n_orth;
+      orth_cols += K;
     } else {
       for (int r = 0; r < B; ++r)
         for (int i = 0; i < K; ++i) {
@@ -603,6 +682,13 @@ int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* label
   inf.restarts = restarts;
   inf.matvecs = matvecs;
   inf.max_resid = maxres;
+  inf.ms_operator = ms_op;
+  inf.ms_orth = ms_orth;
+  inf.n_operator = n_op;
+  inf.n_orth = n_orth;
+  inf.orth_cols = orth_cols;
+  inf.basis = m;
+  inf.block = B;
   int status = converged ? SFAIRSC_OK : SFAIRSC_ERR_NOT_CONVERGED;
   for (int i = 0; i < k; ++i)
     if (c->lam_h[i] >= c->sigma * (1.0 - 1e-8)) status = SFAIRSC_ERR_SHIFT;
@@ -615,6 +701,7 @@ int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* label
     check_cuda(cudaStreamSynchronize(s), "sync");
   }
   launch_embed(n, k, c->X64, c->dinv64, c->normalized, c->Hres, c->colkey, s);
+  c->n_launches += 6;  // scale, colkey init, colmax, argmax, embed, diagnostics
   check_cuda(cudaMemcpyAsync(c->lam_d, c->lam_h.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s), "h2d");
   // diagnostics: max |F^T H| and max |H^T D H - I|
   {
@@ -656,6 +743,7 @@ int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* label
                                        c->opts.kmeans_max_iter, c->labels_d, nullptr, s);
     inf.kmeans_inertia = kr.inertia;
     inf.kmeans_iters = kr.iterations;
+    c->n_launches += kr.launches;
     check_cuda(cudaMemcpyAsync(labels, c->labels_d, sizeof(int32_t) * n,
                                is_device_ptr(labels) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s), "copy labels");
     inf.ms_kmeans = tk.stop(s);
@@ -664,6 +752,7 @@ int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* label
   c->solved = true;
   inf.status = status;
   inf.ms_total = inf.ms_solve + inf.ms_kmeans;
+  inf.n_launches = c->n_launches;
   if (info) *info = inf;
   return status;
 }

@@ -85,7 +85,8 @@ struct OrthPlan {
   int threads = 1024;
   int64_t ldv = 0;
   void* V = nullptr;          // VT, n x ldv columns
-  void* U = nullptr;          // VT, n x B, column-major with ld ldv
+  void* U = nullptr;          // VT, n x 4 row-major: the block being orthogonalised
+  void* Q = nullptr;          // VT, n x 4 row-major: copy of the newest basis block (operator input)
   double* H = nullptr;        // projected matrix, column-major, ld ldh
   int ldh = 0;
   double* partial = nullptr;  // grid * (mmax + 4) * 4
@@ -101,7 +102,9 @@ struct OrthPlan {
 void launch_orth(const OrthPlan& p, VecType vt, int J, int j, int B, cudaStream_t s);
 int orth_max_grid(VecType vt, int B, int threads);
 // V[:, 0:K] = V[:, 0:m] Y (Y: m x K column-major FP64 on device), then V[:, K:K+B] = V[:, m:m+B].
-void launch_restart(VecType vt, int n, void* V, int64_t ldv, int m, int K, int B, const double* Y, cudaStream_t s);
+// Q (n x 4 row-major) receives the carried block too.
+void launch_restart(VecType vt, int n, void* V, int64_t ldv, int m, int K, int B, const double* Y, void* Q,
+                    cudaStream_t s);
 // Fill V[:, 0:B] with a seeded pseudo-random block.
 void launch_random_block(VecType vt, int n, void* V, int64_t ldv, int B, uint64_t seed, cudaStream_t s);
 // X64 = V[:, 0:m] Y (Y: m x k column-major FP64), X64 n x k column-major FP64; V unchanged.
@@ -134,6 +137,7 @@ void launch_backward(int n, const int32_t* row_ptr, const int32_t* col, const vo
 struct KmeansResult {
   double inertia = 0.0;
   int iterations = 0;
+  int launches = 0;
 };
 KmeansResult run_kmeans(int64_t n, int d, const double* X, int kc, uint64_t seed, int n_init, int max_iter,
                         int32_t* labels, double* centroids, cudaStream_t s);

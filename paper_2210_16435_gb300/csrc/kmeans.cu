@@ -473,6 +473,7 @@ KmeansResult run_kmeans(int64_t n64, int d, const double* X, int kc, uint64_t se
     check_cuda(cudaMemcpyAsync(r64, draws.data(), sizeof(unsigned long long) * R * k, cudaMemcpyHostToDevice, s), "h2d");
     check_cuda(cudaMemcpyAsync(centers, first.data(), sizeof(int) * R * k, cudaMemcpyHostToDevice, s), "h2d");
     check_cuda(cudaStreamSynchronize(s), "k-means upload");  // host vectors go out of scope below
+    res.launches = 1 + 4 * (k - 1) + 1;
     for (int t = 1; t < k; ++t) {
       seed_dist_kernel<<<dim3(nb, R), bs, sizeof(float) * d, s>>>(n, d, X32, k, centers, t, D2, blockmax);
       seed_gmax_kernel<<<R, 1024, 0, s>>>(nb, blockmax, gmax);
@@ -512,6 +513,7 @@ KmeansResult run_kmeans(int64_t n64, int d, const double* X, int kc, uint64_t se
     };
     std::vector<int> hdone(R);
     for (int it = 0; it < max_iter; ++it) {
+      res.launches += 3;
       assign();
       update_sums_kernel<<<dim3(unb, R), ub, ssmem, s>>>(n, d, k, X32, lab, xshift, sums, counts, done, rows_per_warp);
       finalize_kernel<<<R, 1024, 0, s>>>(n, d, k, X32, dist, xshift, sums, counts, changed, mu, done, iters, it, max_iter);
@@ -522,6 +524,7 @@ KmeansResult run_kmeans(int64_t n64, int d, const double* X, int kc, uint64_t se
         if (std::all_of(hdone.begin(), hdone.end(), [](int v) { return v != 0; })) break;
       }
     }
+    res.launches += 3;
     own_dist_kernel<<<dim3(nb, R), bs, msmem, s>>>(n, d, k, X32, mu, lab, dist, maxd);
     qsum_all_kernel<<<dim3(nb, R), bs, 0, s>>>(n, dist, maxd, tot);
     check_cuda(cudaGetLastError(), "inertia launch");

@@ -33,6 +33,7 @@ struct OrthArgs {
   int64_t ldv;
   VT* V;
   VT* U;  // row-major n x 4
+  VT* Q;  // row-major n x 4, copy of the new block
   double* H;
   int ldh;
   double* partial;
@@ -363,7 +364,10 @@ __global__ void __launch_bounds__(512, 1) orth_kernel(OrthArgs<VT> a) {
     if (B > 1) tri(Rdiv2, u);
     else u[0] = u[0] / (VT)Rdiv1[0];
 #pragma unroll
-    for (int v = 0; v < B; ++v) a.V[(size_t)r * a.ldv + J + v] = u[v];
+    for (int v = 0; v < B; ++v) {
+      a.V[(size_t)r * a.ldv + J + v] = u[v];
+      a.Q[(size_t)r * 4 + v] = u[v];
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (brk) {
@@ -396,6 +400,7 @@ static void orth_launch_t(const OrthPlan& p, int J, int j, cudaStream_t s) {
   a.ldv = p.ldv;
   a.V = static_cast<VT*>(p.V);
   a.U = static_cast<VT*>(p.U);
+  a.Q = static_cast<VT*>(p.Q);
   a.H = p.H;
   a.ldh = p.ldh;
   a.partial = p.partial;
@@ -465,7 +470,7 @@ int orth_max_grid(VecType vt, int B, int threads) {
 // then V[r, K:K+B] = V[r, m:m+B] (the residual block carried over).
 template <typename VT>
 __global__ void __launch_bounds__(1024) restart_kernel(int n, VT* V, int64_t ldv, int m, int K, int B,
-                                                       const double* __restrict__ Y) {
+                                                       const double* __restrict__ Y, VT* Q) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int width = m + B;
   VT* Vs = reinterpret_cast<VT*>(sm);  // 32 x width
@@ -499,21 +504,26 @@ __global__ void __launch_bounds__(1024) restart_kernel(int n, VT* V, int64_t ldv
     }
   }
   __syncthreads();
-  if (warp < rows && lane < B) V[(size_t)(rbase + warp) * ldv + K + lane] = Vs[warp * width + m + lane];
+  if (warp < rows && lane < B) {
+    const VT x = Vs[warp * width + m + lane];
+    V[(size_t)(rbase + warp) * ldv + K + lane] = x;
+    Q[(size_t)(rbase + warp) * 4 + lane] = x;
+  }
 }
 
-void launch_restart(VecType vt, int n, void* V, int64_t ldv, int m, int K, int B, const double* Y, cudaStream_t s) {
+void launch_restart(VecType vt, int n, void* V, int64_t ldv, int m, int K, int B, const double* Y, void* Q,
+                    cudaStream_t s) {
   const int grid = (n + 31) / 32;
   if (vt == VecType::F64) {
     const size_t smem = sizeof(double) * (32 * (size_t)(m + B) + (size_t)m * 64);
     check_cuda(cudaFuncSetAttribute(restart_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                "restart smem");
-    restart_kernel<double><<<grid, 1024, smem, s>>>(n, (double*)V, ldv, m, K, B, Y);
+    restart_kernel<double><<<grid, 1024, smem, s>>>(n, (double*)V, ldv, m, K, B, Y, (double*)Q);
   } else {
     const size_t smem = sizeof(float) * (32 * (size_t)(m + B) + (size_t)m * 64);
     check_cuda(cudaFuncSetAttribute(restart_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                "restart smem");
-    restart_kernel<float><<<grid, 1024, smem, s>>>(n, (float*)V, ldv, m, K, B, Y);
+    restart_kernel<float><<<grid, 1024, smem, s>>>(n, (float*)V, ldv, m, K, B, Y, (float*)Q);
   }
   check_cuda(cudaGetLastError(), "restart launch");
 }
