@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--block", type=int, default=4)
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 / operator / e2e / CPU side measurements")
+    ap.add_argument("--scale", type=float, default=1.0, help="shrink n of the workload (profiling runs only)")
     return ap.parse_args()
 
 
@@ -51,10 +52,10 @@ def dist_env():
     return world, rank, local
 
 
-def load_workload(name):
+def load_workload(name, scale=1.0):
     from msbm import configs
 
-    c = configs.BUILDERS[name]()
+    c = configs.BUILDERS[name](scale=scale)
     if "graphs" in c:
         raise SystemExit("batched workload: use the batched bench entry")
     return c
@@ -169,9 +170,10 @@ def oracle_estimate(g, k, h, budget_s=12.0, step_model=None):
     reps2 = 0
     t0 = time.perf_counter()
     while reps2 < 2 or (time.perf_counter() - t0 < budget_s / 3 and reps2 < 50):
+        u = w
         for _ in range(2):
-            c = V.T @ w
-            w = w - V @ c
+            c = V.T @ u
+            u = w - V @ c
         reps2 += 1
     t_re = (time.perf_counter() - t0) / reps2
     Y = rng.standard_normal((jbar, k))
@@ -254,7 +256,7 @@ def run_ours(args):
     from paper_2210_16435_gb300 import binding as B
     from paper_2210_16435_gb300.solver import FairSC
 
-    c = load_workload(args.workload)
+    c = load_workload(args.workload, args.scale)
     g, k, h = c["graph"], c["k"], c["h"]
     vdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[c["value_dtype"]]
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -322,7 +324,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "s/solve", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.prec == "mixed" else "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "n": g.n, "nnz": g.nnz, "k": k, "h": h, "prec": args.prec,
+        "config": {"workload": args.workload if args.scale == 1.0 else f"{args.workload}@scale{args.scale}",
+                   "n": g.n, "nnz": g.nnz, "k": k, "h": h, "prec": args.prec,
                    "block": b, "basis": inf["basis"], "tol": 1e-6, "values": c["value_dtype"],
                    "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (CSR 192 MB, basis 400+ MB)"},
         "roofline": roof, "clocks": clk, "gpu_launches": launches,
