@@ -114,6 +114,8 @@ typedef struct {
   int32_t orth_cols;       /* sum over orthogonalisation launches of the basis columns J swept */
   int32_t basis;           /* Krylov basis size m in use */
   int32_t block;           /* Krylov block size b in use */
+  int32_t orth_sweeps;     /* passes over the basis V in all orthogonalisation launches (2 or 3 each) */
+  int32_t reserved[3];
 } sfairsc_info;
 
 typedef struct sfairsc_ctx sfairsc_ctx;

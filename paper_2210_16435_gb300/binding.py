@@ -41,10 +41,11 @@ class Info(ctypes.Structure):
         ("ms_total", ctypes.c_float), ("ms_operator", ctypes.c_float), ("ms_orth", ctypes.c_float),
         ("n_operator", ctypes.c_int32), ("n_orth", ctypes.c_int32), ("n_launches", ctypes.c_int32),
         ("orth_cols", ctypes.c_int32), ("basis", ctypes.c_int32), ("block", ctypes.c_int32),
+        ("orth_sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3),
     ]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
 class SFairSCError(RuntimeError):

@@ -98,6 +98,7 @@ struct sfairsc_ctx {
   unsigned* barrier = nullptr;
   unsigned* err = nullptr;
   int* brk_step = nullptr;
+  int* sweeps = nullptr;
 
   // Krylov workspace
   void* V = nullptr;
@@ -324,8 +325,8 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   const int grid = (int)std::max(1ll, std::min<long long>(gmax, (work + 16383) / 16384));
   c->cta_rows = c->dalloc<int32_t>(grid + 1);
   launch_row_partition(n, c->row_ptr, grid, 16, c->cta_rows, s);
-  const double avg = (double)c->nnz / std::max(n, 1);
-  const int lanes = std::min(32, std::max(4, next_pow2((int)std::ceil(avg / 4.0))));
+  // rows per warp batch: enough batches for every warp of a CTA, at most 32
+  const int batch_rows = (int)std::max(1ll, std::min(32ll, (long long)n / grid / 64));
   const size_t vs = c->vt == VecType::F64 ? 8 : 4;
   c->ytil = c->dalloc<unsigned char>((size_t)n * 4 * vs);
   c->ytil64 = c->dalloc<double>((size_t)n * 4);
@@ -333,6 +334,7 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   c->barrier = c->dalloc<unsigned>(4);
   c->err = c->barrier + 2;
   c->brk_step = c->dalloc<int>(1);
+  c->sweeps = c->dalloc<int>(1);
   check_cuda(cudaMemsetAsync(c->barrier, 0, 4 * sizeof(unsigned), s), "memset");
   OpPlan& o = c->op;
   o.n = n;
@@ -340,7 +342,7 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   o.normalized = c->normalized;
   o.grid = grid;
   o.threads = threads;
-  o.lanes_per_row = lanes;
+  o.batch_rows = batch_rows;
   o.row_ptr = c->row_ptr;
   o.col = c->col;
   o.val = c->val;
@@ -386,9 +388,9 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   c->Yd = c->dalloc<double>((size_t)m * m);
   const int ogmax = orth_max_grid(c->vt, c->B, 512);
   const int ogrid = std::max(1, std::min(ogmax, (n + 511) / 512));
-  const int stride = 8 * 32 * 4 + 16;
+  const int stride = 2 * 128 * 4 + 4 + 32;
   c->orth_partial = c->dalloc<double>((size_t)ogrid * stride);
-  c->orth_coef = c->dalloc<double>(8 * 32 * 4);
+  c->orth_coef = c->dalloc<double>(2 * 128 * 4);
   c->cta_rows_orth = c->dalloc<int32_t>(ogrid + 1);
   std::vector<int32_t> orows(ogrid + 1);
   for (int t = 0; t <= ogrid; ++t) orows[t] = (int32_t)((long long)t * n / ogrid);
@@ -410,6 +412,7 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   q.barrier = c->barrier;
   q.err = c->err;
   q.brk_step = c->brk_step;
+  q.sweeps = c->sweeps;
   check_cuda(cudaMallocHost((void**)&c->Hh, sizeof(double) * c->ldh * m), "pinned allocation");
   check_cuda(cudaMallocHost((void**)&c->Yh, sizeof(double) * m * m), "pinned allocation");
 
@@ -565,6 +568,7 @@ int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* label
   c->n_launches = 0;
   int n_op = 0, n_orth = 0, orth_cols = 0;
   float ms_op = 0.f, ms_orth = 0.f;
+  check_cuda(cudaMemsetAsync(c->sweeps, 0, sizeof(int), s), "memset");
   launch_random_block(c->vt, n, c->U, 4, B, c->opts.seed, s);
   orth(c, 0, -1);
   c->n_launches += 1;
@@ -687,6 +691,11 @@ int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* label
   inf.n_operator = n_op;
   inf.n_orth = n_orth;
   inf.orth_cols = orth_cols;
+  {
+    int sw = 0;
+    check_cuda(cudaMemcpy(&sw, c->sweeps, sizeof(int), cudaMemcpyDeviceToHost), "d2h");
+    inf.orth_sweeps = sw;
+  }
   inf.basis = m;
   inf.block = B;
   int status = converged ? SFAIRSC_OK : SFAIRSC_ERR_NOT_CONVERGED;
@@ -706,7 +715,8 @@ int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* label
   // diagnostics: max |F^T H| and max |H^T D H - I|
   {
     const int h = c->h;
-    launch_diagnostics(n, k, h, c->Hres, c->deg, c->lab, c->params, c->diag_partial, c->diag_blocks, nullptr, s);
+    launch_diagnostics(n, k, h, c->Hres, c->deg, c->lab, c->params, c->diag_partial, c->diag_blocks, nullptr, s,
+                       c->vt == VecType::F64);
     const size_t P = (size_t)h * k + (size_t)k * k;
     std::vector<double> dg((size_t)c->diag_blocks * P);
     check_cuda(cudaMemcpyAsync(dg.data(), c->diag_partial, dg.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "d2h");

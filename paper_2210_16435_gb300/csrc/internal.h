@@ -41,7 +41,7 @@ struct OpPlan {
   int normalized = 1;
   int grid = 0;          // cooperative CTAs
   int threads = 1024;
-  int lanes_per_row = 8; // sub-warp width for the SpMV
+  int batch_rows = 32;   // rows per warp batch in the SpMV sweep (1..32)
   int mode = 0;          // 0: L_n^sigma w, 1: P w
   const int32_t* row_ptr = nullptr;
   const int32_t* col = nullptr;
@@ -95,6 +95,7 @@ struct OrthPlan {
   unsigned* barrier = nullptr;
   unsigned* err = nullptr;
   int* brk_step = nullptr;    // smallest step j whose new block lost rank (atomicMin)
+  int* sweeps = nullptr;      // accumulates the number of passes over V
 };
 // Orthogonalise the B columns in U against V[:, 0:J] (CGS2), record the
 // coefficients in H[0:J, j:j+B], orthonormalise the block (CholQR), store it
@@ -125,7 +126,7 @@ void launch_embed(int n, int k, const double* X, const double* dinv64, int norma
                   unsigned long long* colkey, cudaStream_t s);
 // Fairness and D-orthogonality diagnostics of H.
 void launch_diagnostics(int n, int k, int h, const double* H, const double* deg, const uint8_t* lab,
-                        const double* params, double* partial, int nblocks, double* out, cudaStream_t s);
+                        const double* params, double* partial, int nblocks, double* out, cudaStream_t s, bool fp64);
 
 // Backward SDDMM.
 // grad[e] for every stored entry; partial[b] = per-block sum of the bandwidth terms; A = n-vector workspace.

@@ -25,7 +25,7 @@ namespace sfairsc {
 
 template <typename VT, typename MT>
 struct OpArgs {
-  int n, h, normalized, lanes;
+  int n, h, normalized, batch_rows;
   int mode;  // 0: out = L_n^sigma w;  1: out = P w (projection only)
   const int32_t* __restrict__ row_ptr;
   const int32_t* __restrict__ col;
@@ -67,16 +67,18 @@ __device__ __forceinline__ void load_row(const VT* p, VT (&x)[B]) {
 }
 
 // Adds x (one value per vector, per lane) into lane s's accumulators for the
-// lanes whose label is s.  All 32 lanes must call it.  Sums run in FP64.
+// lanes whose label is s.  All 32 lanes must call it.  The warp sums run in
+// the vector precision (FP64 arithmetic is 1/58 of FP32 on this part); the
+// per-lane running sums are carried into FP64 by the caller.
 template <int B, typename VT>
-__device__ __forceinline__ void warp_group_add(const VT (&x)[B], int label, bool valid, int h, double (&acc)[B]) {
+__device__ __forceinline__ void warp_group_add(const VT (&x)[B], int label, bool valid, int h, VT (&acc)[B]) {
   const int lane = threadIdx.x & 31;
   for (int s = 0; s < h; ++s) {
     const bool mine = valid && label == s;
     if (__ballot_sync(0xffffffffu, mine) == 0u) continue;
 #pragma unroll
     for (int v = 0; v < B; ++v) {
-      double t = warp_allsum(mine ? (double)x[v] : 0.0);
+      const VT t = warp_allsum(mine ? x[v] : VT(0));
       if (lane == s) acc[v] += t;
     }
   }
@@ -173,6 +175,7 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
   double* avec = tot + kMaxGroups * B;                                               // 32*B
   double* coefA = avec + kMaxGroups * B;                                             // 32*B
   double* coefD = coefA + kMaxGroups * B;                                            // 32*B
+  int* rp_s = reinterpret_cast<int*>(coefD + kMaxGroups * B);                         // nwarps * 33
 
   const int r0 = a.cta_rows[blockIdx.x], r1 = a.cta_rows[blockIdx.x + 1];
 
@@ -181,8 +184,13 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
   // ---------------- phase A: group sums of D^{-1/2} w over own rows
   if (grouped) {
     double acc[B];
+    VT accw[B];
 #pragma unroll
-    for (int v = 0; v < B; ++v) acc[v] = 0.0;
+    for (int v = 0; v < B; ++v) {
+      acc[v] = 0.0;
+      accw[v] = VT(0);
+    }
+    int nb = 0;
     for (int base = r0 + warp * 32; base < r1; base += nwarps * 32) {
       const int r = base + lane;
       const bool valid = r < r1;
@@ -197,8 +205,18 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
 #pragma unroll
         for (int v = 0; v < B; ++v) x[v] = VT(0);
       }
-      warp_group_add<B>(x, g, valid, h, acc);
+      warp_group_add<B>(x, g, valid, h, accw);
+      if (++nb == 8) {
+#pragma unroll
+        for (int v = 0; v < B; ++v) {
+          acc[v] += (double)accw[v];
+          accw[v] = VT(0);
+        }
+        nb = 0;
+      }
     }
+#pragma unroll
+    for (int v = 0; v < B; ++v) acc[v] += (double)accw[v];
     block_group_store<B>(acc, h, red, a.partial);
     if (!grid_sync(a.bar, a.err)) return;
     // ---------------- phase B: a = (C^T C)^{-1} C^T w
@@ -220,6 +238,7 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
     }
     return;
   }
+#pragma unroll 4
   for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
     const int g = a.lab[r];
     const VT sc = scale(r);
@@ -232,53 +251,86 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
   if (!grid_sync(a.bar, a.err)) return;
 
   // ---------------- phase C: t = L_n y, written to out; group sums of D^{-1/2} t
+  // Each warp sweeps the stored entries of a 32-row batch as one flat,
+  // coalesced stream (entry e0 + 32u + lane), gathers ytil, and sums the
+  // products per row with a segmented warp scan; the tail lane of every row
+  // segment adds it to that row's shared-memory sum.  The summation tree is
+  // fixed, so results are bitwise reproducible.
   double acc[B];
+  VT accw[B];
 #pragma unroll
-  for (int v = 0; v < B; ++v) acc[v] = 0.0;
-  const int L = a.lanes;
-  const int sub = lane & (L - 1);
-  const int per = 32 / L;
+  for (int v = 0; v < B; ++v) {
+    acc[v] = 0.0;
+    accw[v] = VT(0);
+  }
+  int nbc = 0;
   VT* myrows = rows_s + warp * 32 * B;
-  for (int base = r0 + warp * 32; base < r1; base += nwarps * 32) {
-    for (int pass = 0; pass < L; ++pass) {
-      const int rib = pass * per + lane / L;
-      const int r = base + rib;
-      VT s[B];
+  int* rps = rp_s + warp * 33;
+  constexpr int UCH = B >= 4 ? 2 : 4;  // 32-entry chunks per stage
+  const int RB = a.batch_rows;          // rows per warp batch (1..32)
+  for (int base = r0 + warp * RB; base < r1; base += nwarps * RB) {
+    const int nr = min(RB, r1 - base);
+    if (lane < nr) rps[lane] = __ldg(a.row_ptr + base + lane);
+    if (lane == 0) rps[nr] = __ldg(a.row_ptr + base + nr);
 #pragma unroll
-      for (int v = 0; v < B; ++v) s[v] = VT(0);
-      if (r < r1) {
-        int e = __ldg(a.row_ptr + r) + sub;
-        const int e1 = __ldg(a.row_ptr + r + 1);
-        for (; e + L < e1; e += 2 * L) {
-          const int c0 = __ldg(a.col + e), c1 = __ldg(a.col + e + L);
-          const VT w0 = val_as<VT>(a.val[e]), w1 = val_as<VT>(a.val[e + L]);
-          VT y0[B], y1[B];
-          load_row<VT, B>(a.ytil + (size_t)c0 * B, y0);
-          load_row<VT, B>(a.ytil + (size_t)c1 * B, y1);
+    for (int v = 0; v < B; ++v) myrows[lane * B + v] = VT(0);
+    __syncwarp();
+    const int E0 = rps[0], E1 = rps[nr];
+    int cur = 0;
+    int cc[UCH];
+    VT wv[UCH];
+    auto fetch = [&](int e0, int (&c)[UCH], VT (&w)[UCH]) {
 #pragma unroll
-          for (int v = 0; v < B; ++v) s[v] = fma(w1, y1[v], fma(w0, y0[v], s[v]));
-        }
-        if (e < e1) {
-          const int c0 = __ldg(a.col + e);
-          const VT w0 = val_as<VT>(a.val[e]);
-          VT y0[B];
-          load_row<VT, B>(a.ytil + (size_t)c0 * B, y0);
-#pragma unroll
-          for (int v = 0; v < B; ++v) s[v] = fma(w0, y0[v], s[v]);
-        }
+      for (int u = 0; u < UCH; ++u) {
+        const int e = e0 + 32 * u + lane;
+        const bool ok = e < E1;
+        c[u] = ok ? __ldg(a.col + e) : 0;
+        w[u] = ok ? val_as<VT>(a.val[e]) : VT(0);
       }
-      for (int o = L >> 1; o > 0; o >>= 1) {
+    };
+    fetch(E0, cc, wv);
+    for (int e0 = E0; e0 < E1; e0 += 32 * UCH) {
+      VT y[UCH][B];
 #pragma unroll
-        for (int v = 0; v < B; ++v) s[v] += __shfl_xor_sync(0xffffffffu, s[v], o);
+      for (int u = 0; u < UCH; ++u) load_row<VT, B>(a.ytil + (size_t)cc[u] * B, y[u]);
+      int ncc[UCH];
+      VT nwv[UCH];
+      fetch(e0 + 32 * UCH, ncc, nwv);  // next stage's indices and weights, in flight during this one
+#pragma unroll
+      for (int u = 0; u < UCH; ++u) {
+        const int e = e0 + 32 * u + lane;
+        const bool ok = e < E1;
+        if (ok)
+          while (e >= rps[cur + 1]) ++cur;
+        const int rid = ok ? cur : 32;
+        VT p[B];
+#pragma unroll
+        for (int v = 0; v < B; ++v) p[v] = wv[u] * y[u][v];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int ro = __shfl_up_sync(0xffffffffu, rid, o);
+#pragma unroll
+          for (int v = 0; v < B; ++v) {
+            const VT t = __shfl_up_sync(0xffffffffu, p[v], o);
+            if (lane >= o && ro == rid) p[v] += t;
+          }
+        }
+        const int rn = __shfl_down_sync(0xffffffffu, rid, 1);
+        if (ok && (lane == 31 || rn != rid)) {
+#pragma unroll
+          for (int v = 0; v < B; ++v) myrows[rid * B + v] += p[v];
+        }
+        __syncwarp();
       }
-      if (sub == 0 && r < r1) {
 #pragma unroll
-        for (int v = 0; v < B; ++v) myrows[rib * B + v] = s[v];
+      for (int u = 0; u < UCH; ++u) {
+        cc[u] = ncc[u];
+        wv[u] = nwv[u];
       }
     }
     __syncwarp();
     const int r = base + lane;
-    const bool valid = r < r1;
+    const bool valid = lane < nr;
     VT x[B];
     int g = 0;
     if (valid) {
@@ -297,9 +349,21 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
       for (int v = 0; v < B; ++v) x[v] = VT(0);
     }
     __syncwarp();
-    if (grouped) warp_group_add<B>(x, g, valid, h, acc);
+    if (grouped) {
+      warp_group_add<B>(x, g, valid, h, accw);
+      if (++nbc == 8) {
+#pragma unroll
+        for (int v = 0; v < B; ++v) {
+          acc[v] += (double)accw[v];
+          accw[v] = VT(0);
+        }
+        nbc = 0;
+      }
+    }
   }
   if (!grouped) return;
+#pragma unroll
+  for (int v = 0; v < B; ++v) acc[v] += (double)accw[v];
   block_group_store<B>(acc, h, red, a.partial);
   if (!grid_sync(a.bar, a.err)) return;
 
@@ -324,6 +388,7 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
     }
     __syncthreads();
   }
+#pragma unroll 4
   for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
     const int g = a.lab[r];
     const VT sc = scale(r);
@@ -336,7 +401,8 @@ size_t operator_smem_bytes(int threads, int h, int nvec, VecType vt) {
   const int nwarps = threads / 32;
   const size_t vs = vt == VecType::F64 ? 8 : 4;
   const int P = h * nvec;
-  return vs * nwarps * 32 * nvec + sizeof(double) * ((size_t)nwarps * P + threads + P + 4 * kMaxGroups * nvec) + 64;
+  return vs * nwarps * 32 * nvec + sizeof(double) * ((size_t)nwarps * P + threads + P + 4 * kMaxGroups * nvec) +
+         sizeof(int) * nwarps * 33 + 64;
 }
 
 template <typename VT, typename MT, int B>
@@ -346,7 +412,7 @@ static void launch_t(const OpPlan& p, const void* w, int64_t wrs, int64_t wcs, v
   a.n = p.n;
   a.h = p.h;
   a.normalized = p.normalized;
-  a.lanes = p.lanes_per_row;
+  a.batch_rows = p.batch_rows;
   a.mode = p.mode;
   a.row_ptr = p.row_ptr;
   a.col = p.col;
