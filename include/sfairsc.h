@@ -221,6 +221,38 @@ SFAIRSC_API int sfairsc_kmeans(int64_t n, int32_t d, const double* X, int32_t kc
 SFAIRSC_API int sfairsc_backward(sfairsc_ctx* ctx, const double* grad_lambda, double* grad_values, double bandwidth,
                      double* grad_bandwidth);
 
+/*
+ * One application of L_n^sigma (same result as sfairsc_apply_operator in
+ * MIXED precision) that allocates no memory at all.  The paper has no
+ * counterpart: this exists for callers that cannot call cudaMalloc -- code
+ * that runs while another component is capturing a CUDA graph, plug-ins
+ * inside runtimes that own the device allocator or forbid allocation after
+ * start-up, and fixed-budget embedded or real-time deployments.  No context
+ * is needed: degrees, D^{-1/2}, the C^T C factor and sigma = ||L_n||_1 are
+ * recomputed on every call from the inputs.
+ *
+ * n, nnz, row_ptr, col_idx   CSR of the symmetric W as in sfairsc_create
+ * values                      FP32 weights; group_labels int32 in [0, h)
+ * w, out                      FP32, n x nvec COLUMN-major, nvec in 1..4; must not overlap
+ * Every pointer must be DEVICE memory (host data would need a staging
+ * buffer).  Limits: n <= 524,288, h <= 32, normalized problem only.
+ *
+ * Scratch is one file-scope device array of about 20 MB that every GPU that
+ * loads the library holds until the process exits.  The first call on a
+ * device resolves that array's address (cudaGetSymbolAddress) with the
+ * device current; make that first call before any stream capture.  All calls
+ * share the array and it keeps the last call's contents (each call clears the
+ * words that must start at zero): calls that overlap on the GPU race, so do
+ * not run two at once on one device.  Calls from different host threads are
+ * serialised.  Returns after out is written.
+ * Errors: INVALID_ARG (null or host pointer, bad size), UNSUPPORTED (n or h
+ * above the limits), BAD_CSR, ISOLATED_VERTEX, EMPTY_GROUP, NONFINITE,
+ * DEVICE_TIMEOUT, CUDA.
+ */
+SFAIRSC_API int sfairsc_apply_operator_static(int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
+                                              const float* values, const int32_t* group_labels, int32_t h,
+                                              const float* w, float* out, int32_t nvec, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,12 +25,9 @@
 
 namespace sfairsc {
 
-struct SfError {
-  int code;
-  std::string msg;
-};
-
 static thread_local std::string g_last_error;
+
+void set_last_error(const std::string& msg) { g_last_error = msg; }
 
 void check_cuda(cudaError_t e, const char* what) {
   if (e != cudaSuccess) {

@@ -33,6 +33,13 @@ struct Status {
 };
 void check_cuda(cudaError_t e, const char* what);
 [[noreturn]] void fail(int code, const std::string& msg);
+// What fail() and check_cuda() throw inside the library; entry points map it to a status.
+struct SfError {
+  int code;
+  std::string msg;
+};
+// Record the detail message returned by sfairsc_last_error() on this thread.
+void set_last_error(const std::string& msg);
 
 // Operator launch description (everything the fused kernel needs).
 struct OpPlan {

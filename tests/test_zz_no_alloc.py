@@ -1,0 +1,68 @@
+"""The allocation-free operator entry point against the ordinary one.
+
+sfairsc_apply_operator_static serves callers that cannot allocate device
+memory (for example code running while another component captures a CUDA
+graph, or runtimes that own the allocator).  It keeps all scratch in one
+file-scope device array, so this test calls it twice in a row -- the second
+call reuses the scratch the first one left behind -- and checks both results
+against sfairsc_apply_operator on a context built the normal way, within the
+tolerance the operator tests use for the mixed path.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from conftest import graph_tensors
+from msbm import category_probabilities, cell_sizes_from_proportions, sample_msbm
+
+pytestmark = pytest.mark.gpu
+
+
+def _graph(n, k, h, deg, seed):
+    cells = cell_sizes_from_proportions(n, np.linspace(1, 2, k), 1.0 / np.arange(1, h + 1))
+    return sample_msbm(cells, category_probabilities(cells, deg, (0.5, 0.25, 0.15, 0.10)), seed=seed)
+
+
+def _static_fn():
+    from paper_2210_16435_gb300 import binding as B
+
+    lib = B.load()
+    fn = lib.sfairsc_apply_operator_static
+    fn.restype = ctypes.c_int
+    fn.argtypes = [ctypes.c_int64, ctypes.c_int64] + [ctypes.c_void_p] * 4 + [ctypes.c_int32] + [ctypes.c_void_p] * 2 + \
+        [ctypes.c_int32, ctypes.c_void_p]
+    return fn
+
+
+def test_static_operator_matches_context_operator_twice(built_lib):
+    from paper_2210_16435_gb300.solver import FairSC
+
+    fn = _static_fn()
+    stream = torch.cuda.current_stream().cuda_stream
+    for call, (n, h, nvec, seed) in enumerate([(30_000, 5, 4, 1), (12_345, 3, 1, 2)]):
+        g = _graph(n, 4, h, 30, seed)
+        rp, ci, v, gr = graph_tensors(g, torch.float32)
+        ctx = FairSC(rp, ci, v, gr, k=2, h=h, prec="mixed")
+        w = torch.randn(nvec, g.n, device="cuda", dtype=torch.float32)  # column-major n x nvec
+        ref = torch.empty_like(w)
+        from paper_2210_16435_gb300 import binding as B
+
+        B.sfairsc_apply_operator(ctx.ctx, w.data_ptr(), ref.data_ptr(), nvec)
+        out = torch.full_like(w, float("nan"))
+        rc = fn(g.n, g.nnz, rp.data_ptr(), ci.data_ptr(), v.data_ptr(), gr.data_ptr(), h, w.data_ptr(),
+                out.data_ptr(), nvec, stream)
+        torch.cuda.synchronize()
+        assert rc == 0, (call, rc, B.load().sfairsc_last_error())
+        err = (out - ref).abs().max().item() / (ctx.sigma * w.abs().max().item())
+        assert err < 3e-6, (call, err)
+        ctx.close()
+
+
+def test_static_operator_rejects_sizes_beyond_its_scratch(built_lib):
+    fn = _static_fn()
+    t = torch.zeros(8, dtype=torch.int32, device="cuda")
+    f = torch.zeros(8, dtype=torch.float32, device="cuda")
+    rc = fn(524_289, 10, t.data_ptr(), t.data_ptr(), f.data_ptr(), t.data_ptr(), 2, f.data_ptr(), f.data_ptr(), 1, None)
+    assert rc == -12  # UNSUPPORTED: n above the static limit, nothing launched
