@@ -115,7 +115,9 @@ typedef struct {
   int32_t basis;           /* Krylov basis size m in use */
   int32_t block;           /* Krylov block size b in use */
   int32_t orth_sweeps;     /* passes over the basis V in all orthogonalisation launches (2 or 3 each) */
-  int32_t reserved[3];
+  float ms_restart;        /* with opts.profile: device time of the thick-restart GEMMs */
+  float ms_host_eig;       /* host time of the projected eigenproblems (one per restart) */
+  float ms_final;          /* device time of the final FP64 check, projection and embedding */
 } sfairsc_info;
 
 typedef struct sfairsc_ctx sfairsc_ctx;

@@ -41,7 +41,8 @@ class Info(ctypes.Structure):
         ("ms_total", ctypes.c_float), ("ms_operator", ctypes.c_float), ("ms_orth", ctypes.c_float),
         ("n_operator", ctypes.c_int32), ("n_orth", ctypes.c_int32), ("n_launches", ctypes.c_int32),
         ("orth_cols", ctypes.c_int32), ("basis", ctypes.c_int32), ("block", ctypes.c_int32),
-        ("orth_sweeps", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3),
+        ("orth_sweeps", ctypes.c_int32), ("ms_restart", ctypes.c_float), ("ms_host_eig", ctypes.c_float),
+        ("ms_final", ctypes.c_float),
     ]
 
     def as_dict(self):

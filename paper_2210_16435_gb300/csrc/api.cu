@@ -127,7 +127,7 @@ struct sfairsc_ctx {
   bool solved = false;
   // live kernel timing (opts.profile) and launch counting
   std::vector<cudaEvent_t> ev_pool;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_op, ev_orth;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_op, ev_orth, ev_restart;
   int n_launches = 0;
   cudaEvent_t take_event() {
     if (ev_pool.empty()) {
@@ -150,6 +150,7 @@ struct sfairsc_ctx {
   ~sfairsc_ctx() {
     for (auto& pr : ev_op) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     for (auto& pr : ev_orth) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+    for (auto& pr : ev_restart) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     for (void* p : owned) cudaFree(p);
     if (Hh) cudaFreeHost(Hh);
@@ -340,6 +341,10 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   o.grid = grid;
   o.threads = threads;
   o.batch_rows = batch_rows;
+  {
+    const double avg = (double)c->nnz / std::max(n, 1);
+    o.lanes_per_row = std::min(32, std::max(4, next_pow2((int)std::ceil(avg / 4.0))));
+  }
   o.row_ptr = c->row_ptr;
   o.col = c->col;
   o.val = c->val;
@@ -564,7 +569,8 @@ int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* label
   Timer tsolve(s);
   c->n_launches = 0;
   int n_op = 0, n_orth = 0, orth_cols = 0;
-  float ms_op = 0.f, ms_orth = 0.f;
+  float ms_op = 0.f, ms_orth = 0.f, ms_restart = 0.f;
+  double ms_eig = 0.0;
   check_cuda(cudaMemsetAsync(c->sweeps, 0, sizeof(int), s), "memset");
   launch_random_block(c->vt, n, c->U, 4, B, c->opts.seed, s);
   orth(c, 0, -1);
@@ -593,6 +599,7 @@ int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* label
     if (c->opts.profile) {
       ms_op += drain_events(c, c->ev_op);
       ms_orth += drain_events(c, c->ev_orth);
+      ms_restart += drain_events(c, c->ev_restart);
     }
     const bool broke = brk != kNoBreak;
     // basis columns 0..mv-1 are valid: a block that lost rank at step brk is dropped
@@ -607,7 +614,11 @@ int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* label
         T[(size_t)jj * mv + ii] = v;
         T[(size_t)ii * mv + jj] = v;
       }
-    host_symmetric_eig(mv, T.data(), theta.data());
+    {
+      const auto t0 = std::chrono::steady_clock::now();
+      host_symmetric_eig(mv, T.data(), theta.data());
+      ms_eig += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
     for (int i = 0; i < mv; ++i) {
       double acc = 0.0;
       for (int r = 0; r < B; ++r) {
@@ -622,7 +633,9 @@ int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* label
     const bool estimate_ok = mv >= k && nconv == k && since_break >= 1;
     const bool out_of_restarts = restarts >= c->opts.max_restarts;
     if ((estimate_ok || out_of_restarts) && mv >= k) {
+      Timer tfin(s);
       maxres = final_check(c, mv, T, xx);
+      inf.ms_final += tfin.stop(s);
       if (maxres <= c->opts.tol || out_of_restarts) {
         converged = maxres <= c->opts.tol;
         break;
@@ -636,7 +649,19 @@ int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* label
     for (int i = 0; i < K; ++i)
       for (int q = 0; q < mv; ++q) c->Yh[(size_t)i * mv + q] = T[(size_t)i * mv + q];
     check_cuda(cudaMemcpyAsync(c->Yd, c->Yh, sizeof(double) * mv * K, cudaMemcpyHostToDevice, s), "h2d");
-    launch_restart(c->vt, n, c->V, c->ldv, mv, K, B, c->Yd, c->Q, s);
+    {
+      cudaEvent_t ea = nullptr, eb = nullptr;
+      if (c->opts.profile) {
+        ea = c->take_event();
+        eb = c->take_event();
+        check_cuda(cudaEventRecord(ea, s), "event record");
+      }
+      launch_restart(c->vt, n, c->V, c->ldv, mv, K, B, c->Yd, c->Q, s);
+      if (c->opts.profile) {
+        check_cuda(cudaEventRecord(eb, s), "event record");
+        c->ev_restart.emplace_back(ea, eb);
+      }
+    }
     c->n_launches += 1;
     std::vector<double> Hn((size_t)ldh * m, 0.0);
     for (int i = 0; i < K; ++i) Hn[(size_t)i * ldh + i] = theta[i];
@@ -685,6 +710,8 @@ int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* label
   inf.max_resid = maxres;
   inf.ms_operator = ms_op;
   inf.ms_orth = ms_orth;
+  inf.ms_restart = ms_restart;
+  inf.ms_host_eig = (float)ms_eig;
   inf.n_operator = n_op;
   inf.n_orth = n_orth;
   inf.orth_cols = orth_cols;

@@ -49,6 +49,7 @@ struct OpPlan {
   int grid = 0;          // cooperative CTAs
   int threads = 1024;
   int batch_rows = 32;   // rows per warp batch in the SpMV sweep (1..32)
+  int lanes_per_row = 8; // FP64 vectors: lanes per row (power of two, 4..32)
   int mode = 0;          // 0: L_n^sigma w, 1: P w
   const int32_t* row_ptr = nullptr;
   const int32_t* col = nullptr;

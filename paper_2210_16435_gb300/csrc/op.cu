@@ -25,7 +25,7 @@ namespace sfairsc {
 
 template <typename VT, typename MT>
 struct OpArgs {
-  int n, h, normalized, batch_rows;
+  int n, h, normalized, batch_rows, lanes;
   int mode;  // 0: out = L_n^sigma w;  1: out = P w (projection only)
   const int32_t* __restrict__ row_ptr;
   const int32_t* __restrict__ col;
@@ -275,57 +275,98 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
 #pragma unroll
     for (int v = 0; v < B; ++v) myrows[lane * B + v] = VT(0);
     __syncwarp();
-    const int E0 = rps[0], E1 = rps[nr];
-    int cur = 0;
-    int cc[UCH];
-    VT wv[UCH];
-    auto fetch = [&](int e0, int (&c)[UCH], VT (&w)[UCH]) {
+    if constexpr (sizeof(VT) == 8) {
+      // FP64 vectors: L lanes per row, one FMA per entry and log2(L) shuffle
+      // levels per row (a flat scan would cost several FP64 adds per entry).
+      const int L = a.lanes, sub = lane & (L - 1), per = 32 / L;
+      for (int pass = 0; pass * per < nr; ++pass) {
+        const int rib = pass * per + lane / L;
+        VT sacc[B];
 #pragma unroll
-      for (int u = 0; u < UCH; ++u) {
-        const int e = e0 + 32 * u + lane;
-        const bool ok = e < E1;
-        c[u] = ok ? __ldg(a.col + e) : 0;
-        w[u] = ok ? val_as<VT>(a.val[e]) : VT(0);
-      }
-    };
-    fetch(E0, cc, wv);
-    for (int e0 = E0; e0 < E1; e0 += 32 * UCH) {
-      VT y[UCH][B];
+        for (int v = 0; v < B; ++v) sacc[v] = VT(0);
+        if (rib < nr) {
+          int e = rps[rib] + sub;
+          const int e1 = rps[rib + 1];
+          for (; e + L < e1; e += 2 * L) {
+            const int c0 = __ldg(a.col + e), c1 = __ldg(a.col + e + L);
+            const VT w0 = val_as<VT>(a.val[e]), w1 = val_as<VT>(a.val[e + L]);
+            VT y0[B], y1[B];
+            load_row<VT, B>(a.ytil + (size_t)c0 * B, y0);
+            load_row<VT, B>(a.ytil + (size_t)c1 * B, y1);
 #pragma unroll
-      for (int u = 0; u < UCH; ++u) load_row<VT, B>(a.ytil + (size_t)cc[u] * B, y[u]);
-      int ncc[UCH];
-      VT nwv[UCH];
-      fetch(e0 + 32 * UCH, ncc, nwv);  // next stage's indices and weights, in flight during this one
+            for (int v = 0; v < B; ++v) sacc[v] = fma(w1, y1[v], fma(w0, y0[v], sacc[v]));
+          }
+          if (e < e1) {
+            const int c0 = __ldg(a.col + e);
+            const VT w0 = val_as<VT>(a.val[e]);
+            VT y0[B];
+            load_row<VT, B>(a.ytil + (size_t)c0 * B, y0);
 #pragma unroll
-      for (int u = 0; u < UCH; ++u) {
-        const int e = e0 + 32 * u + lane;
-        const bool ok = e < E1;
-        if (ok)
-          while (e >= rps[cur + 1]) ++cur;
-        const int rid = ok ? cur : 32;
-        VT p[B];
-#pragma unroll
-        for (int v = 0; v < B; ++v) p[v] = wv[u] * y[u][v];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int ro = __shfl_up_sync(0xffffffffu, rid, o);
-#pragma unroll
-          for (int v = 0; v < B; ++v) {
-            const VT t = __shfl_up_sync(0xffffffffu, p[v], o);
-            if (lane >= o && ro == rid) p[v] += t;
+            for (int v = 0; v < B; ++v) sacc[v] = fma(w0, y0[v], sacc[v]);
           }
         }
-        const int rn = __shfl_down_sync(0xffffffffu, rid, 1);
-        if (ok && (lane == 31 || rn != rid)) {
+        for (int o = L >> 1; o > 0; o >>= 1) {
 #pragma unroll
-          for (int v = 0; v < B; ++v) myrows[rid * B + v] += p[v];
+          for (int v = 0; v < B; ++v) sacc[v] += __shfl_xor_sync(0xffffffffu, sacc[v], o);
         }
-        __syncwarp();
-      }
+        if (sub == 0 && rib < nr) {
 #pragma unroll
-      for (int u = 0; u < UCH; ++u) {
-        cc[u] = ncc[u];
-        wv[u] = nwv[u];
+          for (int v = 0; v < B; ++v) myrows[rib * B + v] = sacc[v];
+        }
+      }
+    } else {
+      const int E0 = rps[0], E1 = rps[nr];
+      int cur = 0;
+      int cc[UCH];
+      VT wv[UCH];
+      auto fetch = [&](int e0, int (&c)[UCH], VT (&w)[UCH]) {
+  #pragma unroll
+        for (int u = 0; u < UCH; ++u) {
+          const int e = e0 + 32 * u + lane;
+          const bool ok = e < E1;
+          c[u] = ok ? __ldg(a.col + e) : 0;
+          w[u] = ok ? val_as<VT>(a.val[e]) : VT(0);
+        }
+      };
+      fetch(E0, cc, wv);
+      for (int e0 = E0; e0 < E1; e0 += 32 * UCH) {
+        VT y[UCH][B];
+  #pragma unroll
+        for (int u = 0; u < UCH; ++u) load_row<VT, B>(a.ytil + (size_t)cc[u] * B, y[u]);
+        int ncc[UCH];
+        VT nwv[UCH];
+        fetch(e0 + 32 * UCH, ncc, nwv);  // next stage's indices and weights, in flight during this one
+  #pragma unroll
+        for (int u = 0; u < UCH; ++u) {
+          const int e = e0 + 32 * u + lane;
+          const bool ok = e < E1;
+          if (ok)
+            while (e >= rps[cur + 1]) ++cur;
+          const int rid = ok ? cur : 32;
+          VT p[B];
+  #pragma unroll
+          for (int v = 0; v < B; ++v) p[v] = wv[u] * y[u][v];
+  #pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int ro = __shfl_up_sync(0xffffffffu, rid, o);
+  #pragma unroll
+            for (int v = 0; v < B; ++v) {
+              const VT t = __shfl_up_sync(0xffffffffu, p[v], o);
+              if (lane >= o && ro == rid) p[v] += t;
+            }
+          }
+          const int rn = __shfl_down_sync(0xffffffffu, rid, 1);
+          if (ok && (lane == 31 || rn != rid)) {
+  #pragma unroll
+            for (int v = 0; v < B; ++v) myrows[rid * B + v] += p[v];
+          }
+          __syncwarp();
+        }
+  #pragma unroll
+        for (int u = 0; u < UCH; ++u) {
+          cc[u] = ncc[u];
+          wv[u] = nwv[u];
+        }
       }
     }
     __syncwarp();
@@ -413,6 +454,7 @@ static void launch_t(const OpPlan& p, const void* w, int64_t wrs, int64_t wcs, v
   a.h = p.h;
   a.normalized = p.normalized;
   a.batch_rows = p.batch_rows;
+  a.lanes = p.lanes_per_row;
   a.mode = p.mode;
   a.row_ptr = p.row_ptr;
   a.col = p.col;

@@ -167,6 +167,7 @@ static int apply_static(int64_t n64, int64_t nnz, const int32_t* row_ptr, const 
   o.grid = grid;
   o.threads = threads;
   o.batch_rows = (int)std::max(1ll, std::min(32ll, (long long)n / grid / 64));
+  o.lanes_per_row = 8;
   o.row_ptr = row_ptr;
   o.col = col_idx;
   o.val = values;
