@@ -255,6 +255,98 @@ SFAIRSC_API int sfairsc_apply_operator_static(int64_t n, int64_t nnz, const int3
                                               const float* values, const int32_t* group_labels, int32_t h,
                                               const float* w, float* out, int32_t nvec, void* cuda_stream);
 
+/* ------------------------------------------------------------------ batched form
+ * Many independent problems of Algorithm 3 (steps 2-4: setup, the k smallest
+ * eigenpairs of L_n^sigma, H = D^{-1/2} X) solved by ONE persistent
+ * cooperative kernel launch.  Each graph is the normalized s-FairSC problem
+ * of Sec. 3.4 with its own W (FP32 weights), group labels, h and k.  The
+ * eigensolver is the block (b = 4) form of the restarted Lanczos method: the
+ * operator of Sec. 3.4 (i)-(ii) is applied to 4 vectors at once (an SpMM that
+ * reads the CSR once per 4 vectors), Krylov vectors and the operator run in
+ * FP32, inner products carry in FP64, the projected problem (Rayleigh-Ritz)
+ * and the final residual check run in FP64.  A graph is converged when every
+ * returned pair has ||A x - lambda x|| <= tol * sigma with the FP64 operator.
+ * k-means (step 5) is not part of the batch: call sfairsc_kmeans on H.
+ *
+ * Every pointer in a graph description is DEVICE memory owned by the
+ * caller; row_ptr, col_idx, values and group_labels are read only and must
+ * stay alive and unchanged until sfairsc_batch_destroy.  Outputs (device):
+ * eigenvalues (k doubles, ascending) and, when H is not NULL, H (n x k
+ * doubles, row-major, each column's largest-magnitude entry of X made
+ * positive).  Limits per graph: 16 <= n < 2^30, nnz < 2^31, 1 <= h <= 32,
+ * k <= 28 and k <= n - h + 1.
+ */
+typedef struct {
+  int64_t n, nnz;
+  const int32_t* row_ptr;       /* n + 1 */
+  const int32_t* col_idx;       /* nnz, both triangles, no self loops */
+  const float* values;          /* nnz, w_ij >= 0 */
+  const int32_t* group_labels;  /* n, in [0, h) */
+  int32_t h, k;
+  double* eigenvalues;          /* out: k */
+  double* H;                    /* out: n x k row-major, or NULL */
+} sfairsc_batch_graph;
+
+typedef struct {
+  int32_t status;       /* first non-OK graph status, DEVICE_TIMEOUT, or OK */
+  int32_t converged;    /* graphs that reached tol */
+  int32_t breakdowns;   /* Krylov blocks that lost rank (restarted with fresh vectors) */
+  int32_t grid;         /* CTAs of the launch */
+  int64_t restarts;     /* summed over graphs */
+  int64_t matvecs;      /* operator applications summed over graphs (4 per block) */
+  double max_resid;     /* max over graphs of max_i ||A x_i - lambda_i x_i|| / sigma */
+  double split;         /* schedule: load fraction above which a graph gets a larger team */
+  float ms_solve;       /* device time of the launch */
+  float ms_autotune;    /* host time spent in sfairsc_batch_autotune */
+  int32_t ctas_per_sm;  /* schedule: resident CTAs per SM (1 or 2) */
+  int32_t max_team;     /* schedule: largest team (CTAs working on one graph) */
+  int32_t autotuned;    /* 1 after sfairsc_batch_autotune */
+  int32_t cuda_graph;   /* 1 when the launch sequence replays a captured CUDA graph */
+  int32_t smem_bytes;   /* dynamic shared memory per CTA */
+  int32_t teams[5];     /* teams of 1, 2, 4, 8, 16 CTAs */
+  int32_t reserved[6];
+} sfairsc_batch_info;
+
+typedef struct sfairsc_batch sfairsc_batch;
+
+/* Plan a batch: checks the descriptions, allocates every graph's workspace
+ * (one device arena, about n * (4 (m + 4) + 140) bytes per graph with m the
+ * basis size max(2k + 8, 20)), and builds the schedule from a cost model:
+ * graphs queue largest first, and graphs large against the mean per-CTA load
+ * get teams of 2..16 CTAs that split their rows.  opts: tol, max_restarts,
+ * basis, seed, validate are used (validate 2 also checks symmetry and sorted
+ * columns); NULL gives the defaults.  Errors: INVALID_ARG, K_TOO_LARGE, OOM,
+ * UNSUPPORTED, CUDA.  Per-graph input errors (BAD_CSR, ISOLATED_VERTEX,
+ * EMPTY_GROUP, NONFINITE) are found on the device and reported per graph by
+ * sfairsc_batch_solve. */
+SFAIRSC_API int sfairsc_batch_create(sfairsc_batch** out, int32_t count, const sfairsc_batch_graph* graphs,
+                                     const sfairsc_opts* opts, void* cuda_stream);
+
+/* Autotuner: times every candidate schedule (resident CTAs per SM, largest
+ * team, team threshold) with one full solve each and keeps the fastest; the
+ * outputs hold the last candidate's (identical up to rounding) results. */
+SFAIRSC_API int sfairsc_batch_autotune(sfairsc_batch* batch);
+
+/* Set the schedule by hand: ctas_per_sm 1 or 2 (resident CTAs per SM),
+ * max_team a power of two in 1..16, split >= 0 (a graph moves to the next
+ * larger team while its cost exceeds split x the mean per-CTA load x the team
+ * size; 0 puts every graph on the largest team).  UNSUPPORTED if the kernel
+ * does not fit that many CTAs per SM. */
+SFAIRSC_API int sfairsc_batch_schedule(sfairsc_batch* batch, int32_t ctas_per_sm, int32_t max_team, double split);
+
+/* Solve every graph with one cooperative launch (captured into a CUDA graph
+ * on first use and replayed).  status (host, count entries, nullable)
+ * receives each graph's status.  Returns OK when every graph converged, else
+ * the first failing graph's status (NOT_CONVERGED leaves the best pairs found),
+ * or DEVICE_TIMEOUT if a bounded device wait gave up. */
+SFAIRSC_API int sfairsc_batch_solve(sfairsc_batch* batch, int32_t* status, sfairsc_batch_info* info);
+
+SFAIRSC_API int sfairsc_batch_destroy(sfairsc_batch* batch);
+
+/* create + solve + destroy in one call. */
+SFAIRSC_API int sfairsc_solve_batched(int32_t count, const sfairsc_batch_graph* graphs, const sfairsc_opts* opts,
+                                      int32_t* status, sfairsc_batch_info* info, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

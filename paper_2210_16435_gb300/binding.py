@@ -49,6 +49,30 @@ class Info(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
+class BatchGraph(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p),
+        ("values", ctypes.c_void_p), ("group_labels", ctypes.c_void_p), ("h", ctypes.c_int32), ("k", ctypes.c_int32),
+        ("eigenvalues", ctypes.c_void_p), ("H", ctypes.c_void_p),
+    ]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int32), ("converged", ctypes.c_int32), ("breakdowns", ctypes.c_int32),
+        ("grid", ctypes.c_int32), ("restarts", ctypes.c_int64), ("matvecs", ctypes.c_int64),
+        ("max_resid", ctypes.c_double), ("split", ctypes.c_double), ("ms_solve", ctypes.c_float),
+        ("ms_autotune", ctypes.c_float), ("ctas_per_sm", ctypes.c_int32), ("max_team", ctypes.c_int32),
+        ("autotuned", ctypes.c_int32), ("cuda_graph", ctypes.c_int32), ("smem_bytes", ctypes.c_int32),
+        ("teams", ctypes.c_int32 * 5), ("reserved", ctypes.c_int32 * 6),
+    ]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("reserved", "teams")}
+        d["teams"] = list(self.teams)
+        return d
+
+
 class SFairSCError(RuntimeError):
     def __init__(self, status: int, where: str, detail: str = ""):
         self.status = status
@@ -86,8 +110,18 @@ def load(path: str | None = None):
     lib.sfairsc_solve.argtypes = [vp, vp, vp, vp, ctypes.POINTER(Info)]
     lib.sfairsc_kmeans.argtypes = [i64, i32, vp, i32, u64, i32, i32, vp, vp, vp, vp, vp]
     lib.sfairsc_backward.argtypes = [vp, vp, vp, dbl, vp]
+    lib.sfairsc_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(BatchGraph), ctypes.POINTER(Opts),
+                                         vp]
+    lib.sfairsc_batch_autotune.argtypes = [vp]
+    lib.sfairsc_batch_schedule.argtypes = [vp, i32, i32, dbl]
+    lib.sfairsc_batch_solve.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(BatchInfo)]
+    lib.sfairsc_batch_destroy.argtypes = [vp]
+    lib.sfairsc_solve_batched.argtypes = [i32, ctypes.POINTER(BatchGraph), ctypes.POINTER(Opts),
+                                          ctypes.POINTER(i32), ctypes.POINTER(BatchInfo), vp]
     for f in ("sfairsc_opts_default", "sfairsc_create", "sfairsc_destroy", "sfairsc_get_sigma",
-              "sfairsc_apply_operator", "sfairsc_solve", "sfairsc_kmeans", "sfairsc_backward"):
+              "sfairsc_apply_operator", "sfairsc_solve", "sfairsc_kmeans", "sfairsc_backward",
+              "sfairsc_batch_create", "sfairsc_batch_autotune", "sfairsc_batch_schedule", "sfairsc_batch_solve", "sfairsc_batch_destroy",
+              "sfairsc_solve_batched"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -156,6 +190,55 @@ def sfairsc_backward(ctx, grad_lambda, grad_values, bandwidth=0.0, want_bandwidt
                                  ctypes.byref(gs) if want_bandwidth else None)
     _check(rc, "sfairsc_backward")
     return gs.value if want_bandwidth else None
+
+
+def _graph_array(graphs):
+    arr = (BatchGraph * len(graphs))()
+    for i, g in enumerate(graphs):
+        arr[i] = g
+    return arr
+
+
+def sfairsc_batch_create(graphs, opts=None, stream=None) -> int:
+    """graphs: sequence of BatchGraph (device pointers as integers).  Returns the batch handle."""
+    b = ctypes.c_void_p()
+    arr = _graph_array(graphs)
+    rc = load().sfairsc_batch_create(ctypes.byref(b), len(graphs), arr,
+                                     ctypes.byref(opts) if opts is not None else None, stream)
+    _check(rc, "sfairsc_batch_create")
+    return b.value
+
+
+def sfairsc_batch_autotune(batch) -> None:
+    _check(load().sfairsc_batch_autotune(batch), "sfairsc_batch_autotune")
+
+
+def sfairsc_batch_schedule(batch, ctas_per_sm: int, max_team: int, split: float) -> None:
+    _check(load().sfairsc_batch_schedule(batch, int(ctas_per_sm), int(max_team), float(split)),
+           "sfairsc_batch_schedule")
+
+
+def sfairsc_batch_solve(batch, count: int, allow=(0,)):
+    """Returns (rc, per-graph status list, BatchInfo)."""
+    st = (ctypes.c_int32 * count)()
+    info = BatchInfo()
+    rc = load().sfairsc_batch_solve(batch, st, ctypes.byref(info))
+    _check(rc, "sfairsc_batch_solve", ok=allow)
+    return rc, list(st), info
+
+
+def sfairsc_batch_destroy(batch) -> None:
+    _check(load().sfairsc_batch_destroy(batch), "sfairsc_batch_destroy")
+
+
+def sfairsc_solve_batched(graphs, opts=None, stream=None, allow=(0,)):
+    st = (ctypes.c_int32 * len(graphs))()
+    info = BatchInfo()
+    arr = _graph_array(graphs)
+    rc = load().sfairsc_solve_batched(len(graphs), arr, ctypes.byref(opts) if opts is not None else None, st,
+                                      ctypes.byref(info), stream)
+    _check(rc, "sfairsc_solve_batched", ok=allow)
+    return rc, list(st), info
 
 
 def make_opts(prec="mixed", block=1, tol=1e-6, basis=0, max_restarts=200, sigma=None, seed=1, kmeans_seed=0,

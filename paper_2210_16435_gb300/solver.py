@@ -132,3 +132,58 @@ class FairEigenvalueSum(torch.autograd.Function):
         ctx.solver.close()
         gbw = torch.tensor(gs, dtype=torch.float64, device=gv.device) if ctx.has_bw else None
         return gv.to(ctx.values_dtype), None, None, None, None, None, gbw, None
+
+
+class FairSCBatch:
+    """Many s-FairSC eigenproblems solved by one persistent launch (batched form).
+
+    graphs: sequence of dicts with row_ptr, col_idx (int32), values (float32),
+    groups (int32) CUDA tensors and k, h.  Inputs are borrowed (kept alive
+    here); eigenvalues and H are allocated per graph on the device.
+    """
+
+    def __init__(self, graphs, tol: float = 1e-6, basis: int = 0, max_restarts: int = 200, seed: int = 1,
+                 validate: int = 1, want_H: bool = True, autotune: bool = False,
+                 stream: torch.cuda.Stream | None = None):
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._keep = []
+        self.lam, self.H, descs = [], [], []
+        for g in graphs:
+            rp, ci, va, gr = (g[key].contiguous() for key in ("row_ptr", "col_idx", "values", "groups"))
+            if rp.dtype != torch.int32 or ci.dtype != torch.int32 or gr.dtype != torch.int32:
+                raise TypeError("row_ptr, col_idx and groups must be int32")
+            if va.dtype != torch.float32:
+                raise TypeError("batched values must be float32")
+            if not all(t.is_cuda for t in (rp, ci, va, gr)):
+                raise ValueError("batched inputs must be CUDA tensors")
+            self._keep += [rp, ci, va, gr]
+            n, k, h = rp.numel() - 1, int(g["k"]), int(g["h"])
+            lam = torch.empty(k, dtype=torch.float64, device=self.device)
+            H = torch.empty(n, k, dtype=torch.float64, device=self.device) if want_H else None
+            self.lam.append(lam)
+            self.H.append(H)
+            descs.append(B.BatchGraph(n, ci.numel(), _ptr(rp), _ptr(ci), _ptr(va), _ptr(gr), h, k, _ptr(lam),
+                                      _ptr(H) if H is not None else None))
+        self.count = len(descs)
+        opts = B.make_opts("mixed", 4, tol, basis, max_restarts, None, seed, validate=validate)
+        self.handle = B.sfairsc_batch_create(descs, opts, self.stream.cuda_stream)
+        if autotune:
+            B.sfairsc_batch_autotune(self.handle)
+
+    def solve(self, allow_not_converged: bool = False):
+        """Returns (status list, info dict); results are in self.lam / self.H."""
+        allow = (0, -7) if allow_not_converged else (0,)
+        _, status, info = B.sfairsc_batch_solve(self.handle, self.count, allow=allow)
+        return status, info.as_dict()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            B.sfairsc_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
