@@ -113,6 +113,7 @@ struct Sm {
   double *red, *loc, *tot, *Hm, *A, *E, *Lc;
   float *Yf, *cf;
   double *z, *coefA, *coefD, *av, *cs, *theta, *gram, *R1, *R2, *Rd, *misc;
+  float *coefAf, *coefDf, *Rdf;  // FP32 copies used in the per-row loops
   int* pq;
   unsigned char* ring;
   uint64_t *full, *empty;
@@ -236,7 +237,8 @@ __device__ double cta_sum(Sm& S, double v) {
 // a = (C^T C)^{-1} C^T x with (C^T x)_s = T_s - z_s sum T, and the row
 // coefficients coef[s*4+v] = a_s - z.a (a_{h-1} := 0), so that (C a)_i =
 // d_i^{-1/2} coef[g_i] (Sec. 3.4 (i)).  a_out (nullable) receives a.
-__device__ void solve_groups(const Sm& S, const double* tot, int h, double* a_out, double* coef) {
+__device__ void solve_groups(const Sm& S, const double* tot, int h, double* a_out, double* coef,
+                             float* coef_f = nullptr) {
   const int v = threadIdx.x;
   if (v < kB) {
     const int p = h - 1;
@@ -258,14 +260,17 @@ __device__ void solve_groups(const Sm& S, const double* tot, int h, double* a_ou
     for (int s = 0; s < p; ++s) {
       if (a_out) a_out[s * kB + v] = y[s];
       coef[s * kB + v] = y[s] - za;
+      if (coef_f) coef_f[s * kB + v] = (float)(y[s] - za);
     }
     coef[p * kB + v] = -za;
+    if (coef_f) coef_f[p * kB + v] = (float)-za;
   }
   __syncthreads();
 }
 
 // Row coefficients of C(b - sigma a) (a nullable: C b).
-__device__ void deflate_coef(const Sm& S, int h, double sigma, const double* b, const double* a, double* coef) {
+__device__ void deflate_coef(const Sm& S, int h, double sigma, const double* b, const double* a, double* coef,
+                             float* coef_f = nullptr) {
   const int v = threadIdx.x;
   if (v < kB) {
     const int p = h - 1;
@@ -275,8 +280,12 @@ __device__ void deflate_coef(const Sm& S, int h, double sigma, const double* b, 
       u[q] = b[q * kB + v] - (a ? sigma * a[q * kB + v] : 0.0);
       zu += S.z[q] * u[q];
     }
-    for (int q = 0; q < p; ++q) coef[q * kB + v] = u[q] - zu;
+    for (int q = 0; q < p; ++q) {
+      coef[q * kB + v] = u[q] - zu;
+      if (coef_f) coef_f[q * kB + v] = (float)(u[q] - zu);
+    }
     coef[p * kB + v] = -zu;
+    if (coef_f) coef_f[p * kB + v] = (float)-zu;
   }
   __syncthreads();
 }
@@ -493,60 +502,108 @@ __device__ __forceinline__ void load4(const VT* p, bool l2, VT (&y)[4]) {
 
 // ytil = D^{-1/2} P w for own rows, given the row coefficients of C a in S.coefA.
 template <typename VT>
-__device__ void op_ytil(const Job& J, const Sm& S, int r0, int r1, const VT* w, VT* ytil, const VT* dinv) {
+__device__ void op_ytil(const Job& J, const VT* cA, int r0, int r1, const VT* w, VT* ytil, const VT* dinv) {
   for (int r = r0 + threadIdx.x; r < r1; r += kT) {
     const int g = J.lab[r];
     const VT d = dinv[r];
 #pragma unroll
-    for (int v = 0; v < kB; ++v) ytil[(size_t)r * 4 + v] = d * (w[(size_t)r * 4 + v] - d * (VT)S.coefA[g * kB + v]);
+    for (int v = 0; v < kB; ++v) ytil[(size_t)r * 4 + v] = d * (w[(size_t)r * 4 + v] - d * cA[g * kB + v]);
   }
 }
 
-// t = y - D^{-1/2} W ytil for own rows: `lanes` lanes per row, 4 entries per
-// lane in flight; other CTAs' ytil rows are read through L2 (team) or L1.
+// t = y - D^{-1/2} W ytil for own rows.  `lanes` lanes per row; each lane
+// holds up to U (column, weight) pairs of its row per pass.  The FP32 path is
+// software-pipelined over the warp's row groups: the pairs of the next group
+// and the row bounds of the group after it are loaded while this group's
+// ytil rows are gathered, so a group costs about one memory round trip.
+// Other CTAs' ytil rows are read through L2 (team) or L1.
 template <typename VT>
-__device__ void op_spmm(const Job& J, const Sm& S, int r0, int r1, bool team, const VT* w, const VT* ytil,
+__device__ __forceinline__ void spmm_row_tail(const Job& J, bool team, const VT* ytil, int e, int e1, int Lr,
+                                              VT (&s)[kB]) {
+  for (; e < e1; e += Lr) {
+    const int c = __ldg(J.col + e);
+    const VT w = (VT)__ldg(J.val + e);
+    VT y[4];
+    load4(ytil + (size_t)c * 4, team, y);
+#pragma unroll
+    for (int v = 0; v < kB; ++v) s[v] += w * y[v];
+  }
+}
+
+template <typename VT>
+__device__ void op_spmm(const Job& J, const VT* cA, int r0, int r1, bool team, const VT* w, const VT* ytil,
                         const VT* dinv, VT* t_out) {
+  constexpr int U = sizeof(VT) == 4 ? 8 : 4;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int Lr = J.lanes;
   const int sub = lane & (Lr - 1);
   const int rpw = 32 / Lr;
-  for (int rb = r0 + warp * rpw; rb < r1; rb += kW * rpw) {
+  const int stride = kW * rpw;
+  auto bounds = [&](int rb, int& e, int& e1) {
     const int r = rb + lane / Lr;
-    VT s[kB] = {VT(0), VT(0), VT(0), VT(0)};
     if (r < r1) {
-      const int e1 = __ldg(J.row_ptr + r + 1);
-      for (int e = __ldg(J.row_ptr + r) + sub; e < e1; e += 4 * Lr) {
-        int c[4];
-        VT wv[4];
+      e = __ldg(J.row_ptr + r) + sub;
+      e1 = __ldg(J.row_ptr + r + 1);
+    } else {
+      e = 0;
+      e1 = 0;
+    }
+  };
+  auto fetch = [&](int e, int e1, int (&c)[U], VT (&wv)[U]) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int ee = e + u * Lr;
-          const bool in = ee < e1;
-          c[u] = in ? __ldg(J.col + ee) : 0;
-          wv[u] = in ? (VT)__ldg(J.val + ee) : VT(0);
-        }
+    for (int u = 0; u < U; ++u) {
+      const int ee = e + u * Lr;
+      const bool in = ee < e1;
+      c[u] = in ? __ldg(J.col + ee) : -1;
+      wv[u] = in ? (VT)__ldg(J.val + ee) : VT(0);
+    }
+  };
+  int rb = r0 + warp * rpw;
+  int e_cur = 0, e1_cur = 0, e_nx = 0, e1_nx = 0;
+  int c_cur[U];
+  VT w_cur[U];
+  bounds(rb, e_cur, e1_cur);
+  fetch(e_cur, e1_cur, c_cur, w_cur);
+  bounds(rb + stride, e_nx, e1_nx);
+  for (; rb < r1; rb += stride) {
+    int c_nx[U];
+    VT w_nx[U];
+    fetch(e_nx, e1_nx, c_nx, w_nx);  // next group's pairs, in flight during this group's gathers
+    int e_nn, e1_nn;
+    bounds(rb + 2 * stride, e_nn, e1_nn);
+    VT s[kB] = {VT(0), VT(0), VT(0), VT(0)};
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          VT y[4];
-          load4(ytil + (size_t)c[u] * 4, team, y);
+    for (int u = 0; u < U; ++u) {
+      if (c_cur[u] >= 0) {
+        VT y[4];
+        load4(ytil + (size_t)c_cur[u] * 4, team, y);
 #pragma unroll
-          for (int v = 0; v < kB; ++v) s[v] += wv[u] * y[v];
-        }
+        for (int v = 0; v < kB; ++v) s[v] += w_cur[u] * y[v];
       }
     }
+    if (e_cur + U * Lr < e1_cur) spmm_row_tail(J, team, ytil, e_cur + U * Lr, e1_cur, Lr, s);
     for (int o = Lr >> 1; o > 0; o >>= 1)
 #pragma unroll
       for (int v = 0; v < kB; ++v) s[v] += __shfl_xor_sync(0xffffffffu, s[v], o);
+    const int r = rb + lane / Lr;
     if (r < r1 && sub == 0) {
       const int g = J.lab[r];
       const VT d = dinv[r];
 #pragma unroll
       for (int v = 0; v < kB; ++v) {
-        const VT y = w[(size_t)r * 4 + v] - d * (VT)S.coefA[g * kB + v];
+        const VT y = w[(size_t)r * 4 + v] - d * cA[g * kB + v];
         t_out[(size_t)r * 4 + v] = y - d * s[v];
       }
     }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      c_cur[u] = c_nx[u];
+      w_cur[u] = w_nx[u];
+    }
+    e_cur = e_nx;
+    e1_cur = e1_nx;
+    e_nx = e_nn;
+    e1_nx = e1_nn;
   }
 }
 
@@ -580,6 +637,8 @@ __device__ bool chol4(Sm& S, double* R, const double* ref) {
       }
     }
     S.ints[4] = ok;
+    for (int i = 0; i < 16; ++i) S.Rdf[i] = (float)S.Rd[i];
+    for (int v = 0; v < kB; ++v) S.Rdf[16 + v] = (float)(1.0 / S.Rd[v * kB + v]);
   }
   __syncthreads();
   return S.ints[4] != 0;
@@ -591,8 +650,8 @@ __device__ __forceinline__ void apply_rinv(const Sm& S, float (&u)[4]) {
   for (int v = 0; v < kB; ++v) {
     float s = u[v];
 #pragma unroll
-    for (int q = 0; q < v; ++q) s -= u[q] * (float)S.Rd[q * kB + v];
-    u[v] = s / (float)S.Rd[v * kB + v];
+    for (int q = 0; q < v; ++q) s -= u[q] * S.Rdf[q * kB + v];
+    u[v] = s * S.Rdf[16 + v];
   }
 }
 
@@ -670,10 +729,13 @@ __device__ void gram_pass(const Job& J, Sm& S, Team& T, const Layout& L, int r0,
 // group solve of D^{-1/2} times the new block in S.av / S.coefA for the next
 // operator.  Returns false on a rank loss.
 //
-// The V sweeps map a warp onto 32/LPR rows at a time, LPR lanes per row, lane
-// p of a row holding panel p (columns 4p..4p+3); inner products accumulate in
-// FP32 windows of 32 steps carried by TwoSum and are summed over the row
-// slots of a warp by a TwoSum tree.
+// The V sweeps take 32-row blocks per warp in two phases.  Phase A, one lane
+// per row: finish or update the row of U (the update reads the row's Jc
+// columns of V and the coefficients), store it, and add its Gram entries.
+// Phase B, LPR lanes per row (lane p holds panel p, columns 4p..4p+3): add
+// the row's products to the new coefficients V^T u.  Both phases read V and
+// U with plain coalesced loads (phase B mostly from L1); sums accumulate in
+// FP32 windows carried by TwoSum and are combined over lanes by a TwoSum tree.
 __device__ bool orth_block(const Job& J, Sm& S, Team& T, const Layout& L, long& seq, int r0, int r1, int Jc, int jcol,
                            bool fin, int& sweeps) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -681,17 +743,21 @@ __device__ bool orth_block(const Job& J, Sm& S, Team& T, const Layout& L, long& 
   const int h = J.h;
   const int np = Jc / 4;
   const int x0 = L.jmax * kB;  // extras offset in a slot
-  const int ps = L.stage_rows * 4 + 4, uoff = (L.jmax / 4) * ps;
+  const size_t pan = (size_t)J.n * 4;
   float* U = J.U;
   bool ok = true;
+  (void)seq;
   if (Jc > 0) {
     const int LPR = lanes_for(np), RPW = 32 / LPR;
     const int p = lane & (LPR - 1), ri = lane / LPR;
     const bool own = p < np;
-    // ---- sweep 1: (finish the operator) + c1 = V^T u + input norms
-    {
-      float win[4][kB], nw[kB];
-      Comp acc[4][kB], na[kB];
+    float* uw = reinterpret_cast<float*>(S.red + warp * slot);  // this warp's 32 updated rows (phase A -> B)
+    // sweep(kind): kind 1: finish (fin) + c = V^T u + norms;  kind 2: u -= V cf, c = V^T u, Gram;
+    // kind 3: u -= V cf, Gram.  Leaves the coefficient sums in red[w][c*4+v] and the extras at x0.
+    auto sweep = [&](int kind) {
+      const bool upd = kind >= 2, want_c = kind <= 2;
+      float win[4][kB], gw[10];
+      Comp acc[4][kB], ga[10];
 #pragma unroll
       for (int j = 0; j < 4; ++j)
 #pragma unroll
@@ -700,60 +766,103 @@ __device__ bool orth_block(const Job& J, Sm& S, Team& T, const Layout& L, long& 
           acc[j][v].zero();
         }
 #pragma unroll
-      for (int v = 0; v < kB; ++v) {
-        nw[v] = 0.f;
-        na[v].zero();
+      for (int e = 0; e < 10; ++e) {
+        gw[e] = 0.f;
+        ga[e].zero();
       }
-      int cnt = 0;
-      stream_rows(J, S, L, T.err, seq, r0, r1, np, true, [&](int rg, int nr, const float* st) {
-        for (int i0 = warp * RPW; i0 < nr; i0 += kW * RPW) {
-          const int i = i0 + ri;
-          float u[kB] = {0.f, 0.f, 0.f, 0.f}, x[4] = {0.f, 0.f, 0.f, 0.f};
-          if (i < nr) {
-            const float4 t = *reinterpret_cast<const float4*>(st + uoff + i * 4);
-            u[0] = t.x;
-            u[1] = t.y;
-            u[2] = t.z;
-            u[3] = t.w;
-            if (fin) {
-              const int r = rg + i;
-              const int g = J.lab[r];
-              const float d = J.dinv[r];
+      int nb = 0;
+      for (int rb = r0 + warp * 32; rb < r1; rb += kW * 32) {
+        // ---- phase A: lane = row
+        const int r = rb + lane;
+        float u[kB] = {0.f, 0.f, 0.f, 0.f};
+        if (r < r1) {
+          const float4 t = *reinterpret_cast<const float4*>(U + (size_t)r * 4);
+          u[0] = t.x;
+          u[1] = t.y;
+          u[2] = t.z;
+          u[3] = t.w;
+          if (kind == 1 && fin) {
+            const int g = J.lab[r];
+            const float d = J.dinv[r];
 #pragma unroll
-              for (int v = 0; v < kB; ++v) u[v] -= d * (float)S.coefD[g * kB + v];
-              if (p == 0) *reinterpret_cast<float4*>(U + (size_t)r * 4) = make_float4(u[0], u[1], u[2], u[3]);
+            for (int v = 0; v < kB; ++v) u[v] -= d * S.coefDf[g * kB + v];
+          }
+          if (upd) {
+            float q[kB] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+            for (int pp = 0; pp < np; ++pp) {
+              const float4 x = *reinterpret_cast<const float4*>(J.V + pp * pan + (size_t)r * 4);
+              const float xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                const float4 c4 = *reinterpret_cast<const float4*>(S.cf + (4 * pp + j) * kB);
+                q[0] = fmaf(xs[j], c4.x, q[0]);
+                q[1] = fmaf(xs[j], c4.y, q[1]);
+                q[2] = fmaf(xs[j], c4.z, q[2]);
+                q[3] = fmaf(xs[j], c4.w, q[3]);
+              }
             }
-            if (own) {
-              const float4 t2 = *reinterpret_cast<const float4*>(st + p * ps + i * 4);
-              x[0] = t2.x;
-              x[1] = t2.y;
-              x[2] = t2.z;
-              x[3] = t2.w;
+#pragma unroll
+            for (int v = 0; v < kB; ++v) u[v] -= q[v];
+          } else {
+            // warm L1 with the row's panels for phase B
+            for (int pp = 0; pp < np; ++pp)
+              asm volatile("prefetch.global.L1 [%0];" ::"l"(J.V + pp * pan + (size_t)r * 4));
+          }
+          if (upd || fin) *reinterpret_cast<float4*>(U + (size_t)r * 4) = make_float4(u[0], u[1], u[2], u[3]);
+        }
+        if (kind == 1) {
+          // input norms only: the Gram diagonal
+          gw[0] = fmaf(u[0], u[0], gw[0]);
+          gw[4] = fmaf(u[1], u[1], gw[4]);
+          gw[7] = fmaf(u[2], u[2], gw[7]);
+          gw[9] = fmaf(u[3], u[3], gw[9]);
+        } else {
+          gram_add(gw, u);
+        }
+        if (want_c) *reinterpret_cast<float4*>(uw + lane * 4) = make_float4(u[0], u[1], u[2], u[3]);
+        __syncwarp();
+        // ---- phase B: LPR lanes per row, lane p = panel p
+        if (want_c && own) {
+          const int nrow = min(32, r1 - rb);
+          for (int s0 = 0; s0 < LPR; s0 += 4) {
+            float4 xv[4], uv[4];
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+              const int i = ri + RPW * (s0 + s);
+              const bool in = s0 + s < LPR && i < nrow;
+              xv[s] = in ? *reinterpret_cast<const float4*>(J.V + p * pan + (size_t)(rb + i) * 4)
+                         : make_float4(0.f, 0.f, 0.f, 0.f);
+              uv[s] = in ? *reinterpret_cast<const float4*>(uw + i * 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+              const float xs[4] = {xv[s].x, xv[s].y, xv[s].z, xv[s].w};
+              const float us[4] = {uv[s].x, uv[s].y, uv[s].z, uv[s].w};
+#pragma unroll
+              for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int v = 0; v < kB; ++v) win[j][v] = fmaf(xs[j], us[v], win[j][v]);
             }
           }
+        }
+        __syncwarp();
+        if (++nb == 8) {
 #pragma unroll
           for (int j = 0; j < 4; ++j)
 #pragma unroll
-            for (int v = 0; v < kB; ++v) win[j][v] = fmaf(x[j], u[v], win[j][v]);
-#pragma unroll
-          for (int v = 0; v < kB; ++v) nw[v] = fmaf(u[v], u[v], nw[v]);
-          if (++cnt == 32) {
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-#pragma unroll
-              for (int v = 0; v < kB; ++v) {
-                acc[j][v].add(win[j][v]);
-                win[j][v] = 0.f;
-              }
-#pragma unroll
             for (int v = 0; v < kB; ++v) {
-              na[v].add(nw[v]);
-              nw[v] = 0.f;
+              acc[j][v].add(win[j][v]);
+              win[j][v] = 0.f;
             }
-            cnt = 0;
+#pragma unroll
+          for (int e = 0; e < 10; ++e) {
+            ga[e].add(gw[e]);
+            gw[e] = 0.f;
           }
+          nb = 0;
         }
-      });
+      }
 #pragma unroll
       for (int j = 0; j < 4; ++j)
 #pragma unroll
@@ -762,24 +871,27 @@ __device__ bool orth_block(const Job& J, Sm& S, Team& T, const Layout& L, long& 
           comp_reduce(acc[j][v], LPR);
         }
 #pragma unroll
-      for (int v = 0; v < kB; ++v) {
-        na[v].add(nw[v]);
-        comp_reduce(na[v], LPR);
+      for (int e = 0; e < 10; ++e) {
+        ga[e].add(gw[e]);
+        comp_reduce(ga[e], 1);
       }
-      zero_red(S, slot, x0 + 4);
-      if (ri == 0 && own)
+      zero_red(S, slot, x0 + 10);
+      if (want_c && ri == 0 && own)
 #pragma unroll
         for (int j = 0; j < 4; ++j)
 #pragma unroll
           for (int v = 0; v < kB; ++v) S.red[warp * slot + (4 * p + j) * kB + v] = acc[j][v].value();
       if (lane == 0)
 #pragma unroll
-        for (int v = 0; v < kB; ++v) S.red[warp * slot + x0 + v] = na[v].value();
-    }
-    warps_to_loc(S, slot, x0 + 4);
-    team_reduce(T, S, x0 + 4);
-    ++sweeps;
-    if (threadIdx.x < kB) S.misc[threadIdx.x] = S.tot[x0 + threadIdx.x];
+        for (int e = 0; e < 10; ++e) S.red[warp * slot + x0 + e] = ga[e].value();
+      warps_to_loc(S, slot, x0 + 10);
+      team_reduce(T, S, x0 + 10);
+      ++sweeps;
+    };
+    // ---- sweep 1: (finish the operator) + c1 = V^T u + input norms
+    sweep(1);
+    gram_unpack(S, S.tot + x0);
+    if (threadIdx.x < kB) S.misc[threadIdx.x] = S.gram[threadIdx.x * (kB + 1)];
     for (int i = threadIdx.x; i < Jc * kB; i += kT) {
       S.cf[i] = (float)S.tot[i];
       if (jcol >= 0) S.Hm[(size_t)(i / kB) + (size_t)ldh * (jcol + i % kB)] = S.tot[i];
@@ -787,109 +899,7 @@ __device__ bool orth_block(const Job& J, Sm& S, Team& T, const Layout& L, long& 
     __syncthreads();
     // ---- sweep 2 (u -= V c1; c2 = V^T u; Gram) and, on the DGKS test, sweep 3 (u -= V c2; Gram)
     for (int round = 0; round < 2; ++round) {
-      const bool want_c = round == 0;
-      {
-        float win[4][kB], gw[10];
-        Comp acc[4][kB], ga[10];
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-          for (int v = 0; v < kB; ++v) {
-            win[j][v] = 0.f;
-            acc[j][v].zero();
-          }
-#pragma unroll
-        for (int e = 0; e < 10; ++e) {
-          gw[e] = 0.f;
-          ga[e].zero();
-        }
-        int cnt = 0;
-        stream_rows(J, S, L, T.err, seq, r0, r1, np, true, [&](int rg, int nr, const float* st) {
-          for (int i0 = warp * RPW; i0 < nr; i0 += kW * RPW) {
-            const int i = i0 + ri;
-            float u[kB] = {0.f, 0.f, 0.f, 0.f}, x[4] = {0.f, 0.f, 0.f, 0.f};
-            if (i < nr) {
-              const float4 t = *reinterpret_cast<const float4*>(st + uoff + i * 4);
-              u[0] = t.x;
-              u[1] = t.y;
-              u[2] = t.z;
-              u[3] = t.w;
-              if (own) {
-                const float4 t2 = *reinterpret_cast<const float4*>(st + p * ps + i * 4);
-                x[0] = t2.x;
-                x[1] = t2.y;
-                x[2] = t2.z;
-                x[3] = t2.w;
-              }
-            }
-            // this lane's 4 columns of V c, summed over the row's LPR lanes
-            float q[kB] = {0.f, 0.f, 0.f, 0.f};
-            if (own)
-#pragma unroll
-              for (int j = 0; j < 4; ++j) {
-                const float4 c4 = *reinterpret_cast<const float4*>(S.cf + (4 * p + j) * kB);
-                q[0] = fmaf(x[j], c4.x, q[0]);
-                q[1] = fmaf(x[j], c4.y, q[1]);
-                q[2] = fmaf(x[j], c4.z, q[2]);
-                q[3] = fmaf(x[j], c4.w, q[3]);
-              }
-            for (int o = 1; o < LPR; o <<= 1)
-#pragma unroll
-              for (int v = 0; v < kB; ++v) q[v] += __shfl_xor_sync(0xffffffffu, q[v], o);
-#pragma unroll
-            for (int v = 0; v < kB; ++v) u[v] -= q[v];
-            if (i < nr && p == 0)
-              *reinterpret_cast<float4*>(U + (size_t)(rg + i) * 4) = make_float4(u[0], u[1], u[2], u[3]);
-            if (want_c)
-#pragma unroll
-              for (int j = 0; j < 4; ++j)
-#pragma unroll
-                for (int v = 0; v < kB; ++v) win[j][v] = fmaf(x[j], u[v], win[j][v]);
-            gram_add(gw, u);
-            if (++cnt == 32) {
-              if (want_c)
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-#pragma unroll
-                  for (int v = 0; v < kB; ++v) {
-                    acc[j][v].add(win[j][v]);
-                    win[j][v] = 0.f;
-                  }
-#pragma unroll
-              for (int e = 0; e < 10; ++e) {
-                ga[e].add(gw[e]);
-                gw[e] = 0.f;
-              }
-              cnt = 0;
-            }
-          }
-        });
-        if (want_c)
-#pragma unroll
-          for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int v = 0; v < kB; ++v) {
-              acc[j][v].add(win[j][v]);
-              comp_reduce(acc[j][v], LPR);
-            }
-#pragma unroll
-        for (int e = 0; e < 10; ++e) {
-          ga[e].add(gw[e]);
-          comp_reduce(ga[e], LPR);
-        }
-        zero_red(S, slot, x0 + 10);
-        if (want_c && ri == 0 && own)
-#pragma unroll
-          for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int v = 0; v < kB; ++v) S.red[warp * slot + (4 * p + j) * kB + v] = acc[j][v].value();
-        if (lane == 0)
-#pragma unroll
-          for (int e = 0; e < 10; ++e) S.red[warp * slot + x0 + e] = ga[e].value();
-      }
-      warps_to_loc(S, slot, x0 + 10);
-      team_reduce(T, S, x0 + 10);
-      ++sweeps;
+      sweep(round == 0 ? 2 : 3);
       gram_unpack(S, S.tot + x0);
       int again = 0;
       for (int v = 0; v < kB; ++v)
@@ -922,9 +932,12 @@ __device__ bool orth_block(const Job& J, Sm& S, Team& T, const Layout& L, long& 
   warps_to_loc(S, slot, h * kB);
   team_reduce(T, S, h * kB);
   if (h > 1) {
-    solve_groups(S, S.tot, h, S.av, S.coefA);
+    solve_groups(S, S.tot, h, S.av, S.coefA, S.coefAf);
   } else {
-    for (int i = threadIdx.x; i < kMaxH * kB; i += kT) S.coefA[i] = S.av[i] = 0.0;
+    for (int i = threadIdx.x; i < kMaxH * kB; i += kT) {
+      S.coefA[i] = S.av[i] = 0.0;
+      S.coefAf[i] = 0.f;
+    }
     __syncthreads();
   }
   if (threadIdx.x == 0 && jcol >= 0) {
@@ -943,9 +956,9 @@ __device__ bool orth_block(const Job& J, Sm& S, Team& T, const Layout& L, long& 
 // coefficients of C(b - sigma a); orth_block's first sweep subtracts them.
 __device__ void operator_f32(const Job& J, Sm& S, Team& T, const Layout& L, int r0, int r1, int pin, double sigma) {
   const float* w = J.V + (size_t)pin * J.n * 4;
-  op_ytil<float>(J, S, r0, r1, w, J.ytil, J.dinv);
+  op_ytil<float>(J, S.coefAf, r0, r1, w, J.ytil, J.dinv);
   team_barrier(T, S);
-  op_spmm<float>(J, S, r0, r1, T.size > 1, w, J.ytil, J.dinv, J.U);
+  op_spmm<float>(J, S.coefAf, r0, r1, T.size > 1, w, J.ytil, J.dinv, J.U);
   __syncthreads();
   if (J.h > 1) {
     group_sums_f32(S, L.slot, r0, r1, J.h, J.lab, [&](int r, float(&x)[kB]) {
@@ -958,10 +971,13 @@ __device__ void operator_f32(const Job& J, Sm& S, Team& T, const Layout& L, int 
     });
     warps_to_loc(S, L.slot, J.h * kB);
     team_reduce(T, S, J.h * kB);
-    solve_groups(S, S.tot, J.h, S.coefD, S.cs);         // b into coefD
-    deflate_coef(S, J.h, sigma, S.coefD, S.av, S.coefD);  // same thread reads b before writing
+    solve_groups(S, S.tot, J.h, S.coefD, S.cs);                   // b into coefD
+    deflate_coef(S, J.h, sigma, S.coefD, S.av, S.coefD, S.coefDf);  // same thread reads b before writing
   } else {
-    for (int i = threadIdx.x; i < kMaxH * kB; i += kT) S.coefD[i] = 0.0;
+    for (int i = threadIdx.x; i < kMaxH * kB; i += kT) {
+      S.coefD[i] = 0.0;
+      S.coefDf[i] = 0.f;
+    }
     __syncthreads();
   }
 }
@@ -985,66 +1001,145 @@ __device__ __forceinline__ void rr_pair(int rr, int t, int N, int& p, int& q) {
   }
 }
 
-// Eigen-decomposition of the symmetric N x N matrix S.A (column-major), N even:
-// eigenvalues ascending in S.theta, eigenvectors in the columns of S.A.
-// Rotation angles as in Golub and Van Loan, Matrix Computations, Sec. 8.5.
-__device__ void jacobi_eig(Sm& S, int N) {
-  double* A = S.A;
-  double* E = S.E;
+// Parallel cyclic Jacobi sweeps on the symmetric N x N matrix A (column-major,
+// element type T), rotations accumulated into E.  Stops when the squared
+// off-diagonal Frobenius norm is at most tol times the total, or after maxs
+// sweeps.  Rotations with |a_pq| <= skip * sqrt(|a_pp a_qq|) are skipped
+// (threshold Jacobi).  Rotation angles as in Golub and Van Loan, Matrix
+// Computations, Sec. 8.5.
+template <typename T>
+__device__ void jacobi_sweeps(Sm& S, T* A, T* E, int N, int maxs, double tol, double skip) {
   const int half = N / 2;
-  for (int i = threadIdx.x; i < N * N; i += kT) E[i] = (i % N == i / N) ? 1.0 : 0.0;
-  __syncthreads();
-  for (int sweep = 0; sweep < kJacobiSweeps; ++sweep) {
+  for (int sweep = 0; sweep < maxs; ++sweep) {
     double off = 0.0, tot = 0.0;
     for (int i = threadIdx.x; i < N * N; i += kT) {
-      const double x = A[i] * A[i];
+      const double x = (double)A[i] * (double)A[i];
       tot += x;
       if (i % N != i / N) off += x;
     }
     off = cta_sum(S, off);
     tot = cta_sum(S, tot);
-    if (!(off > 1e-30 * tot)) break;
+    if (!(off > tol * tot)) break;
     for (int rr = 0; rr < N - 1; ++rr) {
       if ((int)threadIdx.x < half) {
         int p, q;
         rr_pair(rr, threadIdx.x, N, p, q);
-        const double apq = A[p + q * N];
-        double c = 1.0, s = 0.0;
-        if (apq != 0.0) {
-          const double tau = (A[q + q * N] - A[p + p * N]) / (2.0 * apq);
-          const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-          c = 1.0 / sqrt(1.0 + t * t);
+        const T apq = A[p + q * N];
+        T c = T(1), s = T(0);
+        if (fabs((double)apq) > skip * sqrt(fabs((double)A[p + p * N] * (double)A[q + q * N])) + 1e-300) {
+          const T tau = (A[q + q * N] - A[p + p * N]) / (T(2) * apq);
+          const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
+          c = T(1) / sqrt(T(1) + t * t);
           s = t * c;
         }
-        S.cs[2 * threadIdx.x] = c;
-        S.cs[2 * threadIdx.x + 1] = s;
+        S.cs[2 * threadIdx.x] = (double)c;
+        S.cs[2 * threadIdx.x + 1] = (double)s;
         S.pq[2 * threadIdx.x] = p;
         S.pq[2 * threadIdx.x + 1] = q;
       }
       __syncthreads();
       for (int i = threadIdx.x; i < half * N; i += kT) {  // rows p and q
         const int t = i / N, col = i % N;
+        const T s = (T)S.cs[2 * t + 1];
+        if (s == T(0)) continue;
+        const T c = (T)S.cs[2 * t];
         const int p = S.pq[2 * t], q = S.pq[2 * t + 1];
-        const double c = S.cs[2 * t], s = S.cs[2 * t + 1];
-        const double xp = A[p + col * N], xq = A[q + col * N];
+        const T xp = A[p + col * N], xq = A[q + col * N];
         A[p + col * N] = c * xp - s * xq;
         A[q + col * N] = s * xp + c * xq;
       }
       __syncthreads();
       for (int i = threadIdx.x; i < half * N; i += kT) {  // columns p and q, of A and of E
         const int t = i / N, row = i % N;
+        const T s = (T)S.cs[2 * t + 1];
+        if (s == T(0)) continue;
+        const T c = (T)S.cs[2 * t];
         const int p = S.pq[2 * t], q = S.pq[2 * t + 1];
-        const double c = S.cs[2 * t], s = S.cs[2 * t + 1];
-        const double xp = A[row + p * N], xq = A[row + q * N];
-        A[row + p * N] = row == q ? 0.0 : c * xp - s * xq;
-        A[row + q * N] = row == p ? 0.0 : s * xp + c * xq;
-        const double ep = E[row + p * N], eq = E[row + q * N];
+        const T xp = A[row + p * N], xq = A[row + q * N];
+        A[row + p * N] = row == q ? T(0) : c * xp - s * xq;
+        A[row + q * N] = row == p ? T(0) : s * xp + c * xq;
+        const T ep = E[row + p * N], eq = E[row + q * N];
         E[row + p * N] = c * ep - s * eq;
         E[row + q * N] = s * ep + c * eq;
       }
       __syncthreads();
     }
   }
+}
+
+// Eigen-decomposition of the symmetric N x N matrix S.A (column-major, FP64),
+// N even: eigenvalues ascending in S.theta, eigenvectors in the columns of S.A.
+// Jacobi sweeps first run in FP32 on a copy (this GPU's FP32 rate is far above
+// its FP64 rate); the FP32 eigenvector matrix is then made orthonormal in
+// FP64 (one Newton-Schulz step, E <- E (3I - E^T E) / 2), the FP64 matrix is
+// transformed to E^T A E, and FP64 Jacobi sweeps finish the diagonalisation
+// to FP64 accuracy.  Scratch: S.Yf (N^2 floats) and the ring (2 N^2 floats, then N^2 doubles).
+__device__ void jacobi_eig(Sm& S, int N) {
+  double* A = S.A;
+  double* E = S.E;
+  float* Af = S.Yf;
+  float* Ef = reinterpret_cast<float*>(S.ring);
+  double* T2 = reinterpret_cast<double*>(S.ring);
+  const int NN = N * N;
+  for (int i = threadIdx.x; i < NN; i += kT) {
+    Af[i] = (float)A[i];
+    Ef[i] = (i % N == i / N) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  jacobi_sweeps<float>(S, Af, Ef, N, 12, 1e-13, 1e-9);
+  for (int i = threadIdx.x; i < NN; i += kT) E[i] = (double)Ef[i];
+  __syncthreads();
+  // G = E^T E, then M = (3I - G) / 2 into T2
+  for (int i = threadIdx.x; i < NN; i += kT) {
+    const int a = i % N, b = i / N;
+    double g = 0.0;
+    for (int r = 0; r < N; ++r) g = fma(E[r + a * N], E[r + b * N], g);
+    T2[i] = (a == b ? 1.5 : 0.0) - 0.5 * g;
+  }
+  __syncthreads();
+  // E <- E M, one row per warp, in place
+  {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int r = warp; r < N; r += kW) {
+      double o0 = 0.0, o1 = 0.0;
+      for (int kk = 0; kk < N; ++kk) {
+        const double e = E[r + kk * N];
+        if (lane < N) o0 = fma(e, T2[kk + lane * N], o0);
+        if (lane + 32 < N) o1 = fma(e, T2[kk + (lane + 32) * N], o1);
+      }
+      __syncwarp();
+      if (lane < N) E[r + lane * N] = o0;
+      if (lane + 32 < N) E[r + (lane + 32) * N] = o1;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  // B = A E into T2, then A <- E^T B
+  for (int i = threadIdx.x; i < NN; i += kT) {
+    const int a = i % N, b = i / N;
+    double x = 0.0;
+    for (int kk = 0; kk < N; ++kk) x = fma(A[a + kk * N], E[kk + b * N], x);
+    T2[i] = x;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < NN; i += kT) {
+    const int a = i % N, b = i / N;
+    double x = 0.0;
+    for (int kk = 0; kk < N; ++kk) x = fma(E[kk + a * N], T2[kk + b * N], x);
+    A[i] = x;
+  }
+  __syncthreads();
+  // symmetrise (E^T A E is symmetric up to rounding), then FP64 sweeps
+  for (int i = threadIdx.x; i < NN; i += kT) {
+    const int a = i % N, b = i / N;
+    if (a < b) {
+      const double m = 0.5 * (A[a + b * N] + A[b + a * N]);
+      A[a + b * N] = m;
+      A[b + a * N] = m;
+    }
+  }
+  __syncthreads();
+  jacobi_sweeps<double>(S, A, E, N, kJacobiSweeps, 1e-28, 1e-18);
   // ascending order, ties by index
   if ((int)threadIdx.x < N) {
     const int i = threadIdx.x;
@@ -1058,7 +1153,7 @@ __device__ void jacobi_eig(Sm& S, int N) {
     S.theta[rank] = di;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < N * N; i += kT) {
+  for (int i = threadIdx.x; i < NN; i += kT) {
     const int row = i % N, col = i / N;
     A[row + S.pq[col] * N] = E[row + col * N];
   }
@@ -1333,7 +1428,7 @@ __device__ double final_check4(const Job& J, Sm& S, Team& T, const Layout& L, lo
   __syncthreads();
   for (int i = tid; i < kMaxH * kB; i += kT) S.coefA[i] = 0.0;  // y = P x = x
   team_barrier(T, S);
-  op_spmm<double>(J, S, r0, r1, T.size > 1, J.X, J.ytil64, J.dinv64, J.AX);
+  op_spmm<double>(J, S.coefA, r0, r1, T.size > 1, J.X, J.ytil64, J.dinv64, J.AX);
   __syncthreads();
   if (h > 1) {
     group_sums_f64(S, slot, r0, r1, h, J.lab, [&](int r, double(&x)[kB]) {
@@ -1587,9 +1682,12 @@ __device__ void solve_graph(const Job& J, Stat* st, const Params& prm, Sm& S, Te
       warps_to_loc(S, slot, h * kB);
       team_reduce(T, S, h * kB);
       if (h > 1) {
-        solve_groups(S, S.tot, h, S.av, S.coefA);
+        solve_groups(S, S.tot, h, S.av, S.coefA, S.coefAf);
       } else {
-        for (int i = tid; i < kMaxH * kB; i += kT) S.coefA[i] = S.av[i] = 0.0;
+        for (int i = tid; i < kMaxH * kB; i += kT) {
+          S.coefA[i] = S.av[i] = 0.0;
+          S.coefAf[i] = 0.f;
+        }
         __syncthreads();
       }
     } else {
@@ -1620,6 +1718,7 @@ __global__ void __launch_bounds__(kT, MINB) batched_kernel(const __grid_constant
   __shared__ int ints[16];
   __shared__ double smallbuf[kMaxH + 4 * kMaxH * kB + 2 * kMaxM + 16 * 5];
   __shared__ int pq[2 * kMaxM];
+  __shared__ float smallf[2 * kMaxH * kB + 20];
   const Layout& L = P.L;
   Sm S;
   S.red = reinterpret_cast<double*>(base + L.red);
@@ -1655,6 +1754,9 @@ __global__ void __launch_bounds__(kT, MINB) batched_kernel(const __grid_constant
   sb += 16;
   S.misc = sb;
   S.pq = pq;
+  S.coefAf = smallf;
+  S.coefDf = smallf + kMaxH * kB;
+  S.Rdf = smallf + 2 * kMaxH * kB;
   S.full = full;
   S.empty = empty;
   S.ints = ints;
@@ -1725,7 +1827,8 @@ Layout make_layout(int mmax, int stage_target) {
   L.yf = take(mmax * mmax * 4);
   L.cf = take(L.jmax * kB * 4);
   L.lc = take(kMaxH * kMaxH * 8);
-  L.ring = take(kStages * L.stage_floats * 4);
+  // the ring also serves as Jacobi scratch: 2 mmax^2 floats (or mmax^2 doubles)
+  L.ring = take(std::max(kStages * L.stage_floats, 2 * mmax * mmax) * 4);
   L.total = off + 128;
   return L;
 }
@@ -1986,8 +2089,8 @@ BatchPlan* batch_create(int count, const sfairsc_batch_graph* graphs, const sfai
     J.m = m;
     J.ldv = m + bat::kB;
     const double avg = (double)G.nnz / (double)G.n;
-    int lanes = 4;
-    while (lanes < 32 && lanes * 4 < avg) lanes *= 2;
+    int lanes = 2;
+    while (lanes < 32 && lanes * 8 < avg) lanes *= 2;
     J.lanes = lanes;
     J.row_ptr = G.row_ptr;
     J.col = G.col_idx;
