@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--block", type=int, default=4)
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 / operator / e2e / CPU side measurements")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 256-graph batched measurement")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink n of the workload (profiling runs only)")
     return ap.parse_args()
 
@@ -123,11 +124,13 @@ def operator_bytes(n, nnz, s_v, s_x, b):
     return 4 * (n + 1) + nnz * (4 + s_v) + n * (2 * b * s_x + 1 + s_x)
 
 
-def orth_bytes(n, sum_cols, launches, s_x, b):
-    """Algorithmic bytes of the CGS2 launches: V[:, 0:J] is read three times per
-    launch (coefficients, first update fused with the second coefficients,
-    second update), the new block is read once and written once."""
-    return 3 * n * s_x * sum_cols + launches * 2 * n * b * s_x
+def orth_bytes(n, sum_cols, launches, sweeps, s_x, b):
+    """Algorithmic bytes of the Gram-Schmidt launches: V[:, 0:J] is read once
+    per sweep (2 sweeps: coefficients, then the update fused with the second
+    coefficients and the Gram matrix; 3 when the DGKS test asks for the second
+    projection), the new block is read once and written once.  sweeps / launches
+    is the measured mean number of sweeps per launch."""
+    return (sweeps / max(1, launches)) * n * s_x * sum_cols + launches * 2 * n * b * s_x
 
 
 def measured_peaks():
@@ -137,6 +140,117 @@ def measured_peaks():
             d = json.load(f)
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def batched_basis(n, k):
+    """Basis size m and thick-restart size K of one graph of the batched solver."""
+    m = max(2 * k + 8, 20)
+    m = (m + 3) // 4 * 4
+    m = min(m, min(60, (n // 4) * 4 - 4))
+    K = k + (m - k) // 2
+    K = max(K // 4 * 4, (k + 3) // 4 * 4)
+    K = min(K, m - 4)
+    return m, K
+
+
+def batched_bytes(n, nnz, k, matvecs, restarts):
+    """Algorithmic HBM bytes of one graph's batched solve (FP32 vectors, FP32 weights).
+
+    Per block step (4 operator applications): the CSR once (4(n+1) + 8 nnz),
+    the input panel, the output block, D^{-1/2} and the labels (n (16 + 16 + 4
+    + 1)); classical Gram-Schmidt at its minimum, V[:, 0:J] read twice (8 n J)
+    plus the new panel written (16 n), J averaged over a restart cycle.  Per
+    restart the basis is read once and the kept columns written once."""
+    m, K = batched_basis(n, k)
+    steps = matvecs // 4
+    jbar = (K + m) / 2 + 2
+    per_step = 4 * (n + 1) + 8 * nnz + n * 37 + 8 * n * jbar + 16 * n
+    per_restart = 4 * n * (m + K)
+    return steps * per_step + restarts * per_restart
+
+
+def batched_extra(dev, peak, scale=1.0, sequential=True, seq_sample=None):
+    """The batched form on the 256-graph workload: one persistent launch per
+    solve, default schedule and autotuned, against sequential solves of the
+    same graphs through the single-graph API (FP64 block 1, and mixed block 4)."""
+    import numpy as np
+    import torch
+
+    from msbm import configs
+    from paper_2210_16435_gb300.solver import FairSC, FairSCBatch
+
+    t0 = time.perf_counter()
+    c = configs.msbm_batch256(scale=scale)
+    gen_s = time.perf_counter() - t0
+    T = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    ents = [{"row_ptr": T(x["graph"].row_ptr, torch.int32), "col_idx": T(x["graph"].col_idx, torch.int32),
+             "values": T(x["graph"].values, torch.float32), "groups": T(x["graph"].groups, torch.int32),
+             "k": x["k"], "h": x["h"]} for x in c["graphs"]]
+    b = FairSCBatch(ents)
+    b.solve()
+    reps = 3
+    ms_def = [b.solve()[1]["ms_solve"] for _ in range(reps)]
+    st, info_def = b.solve()
+    t0 = time.perf_counter()
+    from paper_2210_16435_gb300 import binding as B
+
+    B.sfairsc_batch_autotune(b.handle)
+    tune_s = time.perf_counter() - t0
+    ms_at = [b.solve()[1]["ms_solve"] for _ in range(reps)]
+    st, info = b.solve()
+    restarts, matvecs, resid = b.stats()
+    b.close()
+    tot_bytes = sum(batched_bytes(x["graph"].n, x["graph"].nnz, x["k"], mv, rs)
+                    for x, mv, rs in zip(c["graphs"], matvecs, restarts))
+    ms = min(ms_at)
+    gbs = tot_bytes / (ms * 1e6)
+    # sequential solves through the single-graph API (every graph, or a sample scaled up)
+    idx = list(range(len(ents))) if seq_sample is None else seq_sample
+    seq = {}
+    for prec, blk in ((("fp64", 1), ("mixed", 4)) if sequential else ()):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        nconv = 0
+        for i in idx:
+            e = ents[i]
+            s = FairSC(e["row_ptr"], e["col_idx"], e["values"], e["groups"], k=e["k"], h=e["h"], prec=prec, block=blk)
+            _, _, _, inf = s.solve(want_labels=False, allow_not_converged=True)
+            nconv += s.status == 0
+            s.close()
+        torch.cuda.synchronize()
+        el = (time.perf_counter() - t1) * len(ents) / len(idx)
+        seq[f"sequential_{prec}_block{blk}_s"] = el
+        seq[f"sequential_{prec}_converged"] = f"{nconv}/{len(idx)}"
+    return {
+        "workload": "msbm_batch256 (256 m-SBM graphs, n log-uniform 1k-64k, k 3-10, h 2-6, degree 16-64, FP32 weights)",
+        "graphs": len(ents), "sum_n": int(sum(x["graph"].n for x in c["graphs"])),
+        "sum_nnz": int(sum(x["graph"].nnz for x in c["graphs"])),
+        "solve_s": ms / 1e3, "solve_s_default_schedule": min(ms_def) / 1e3, "autotune_s": tune_s,
+        "converged": info["converged"], "max_resid": info["max_resid"], "restarts": info["restarts"],
+        "matvecs": info["matvecs"], "schedule": {"ctas_per_sm": info["ctas_per_sm"], "max_team": info["max_team"],
+                                                  "split": info["split"], "teams_1_2_4_8_16": info["teams"],
+                                                  "grid": info["grid"]},
+        "cuda_graph": info["cuda_graph"], "gpu_launches_per_solve": 1,
+        "roofline": {"kernel": "batched_kernel (persistent, all graphs)", "bound": "hbm", "achieved": gbs,
+                     "peak": peak, "unit": "GB/s", "frac": gbs / peak, "traffic": None,
+                     "bytes_per_launch": tot_bytes, "ms_per_launch": ms},
+        **seq, "speedup_vs_sequential_fp64": (seq["sequential_fp64_block1_s"] / (ms / 1e3)) if seq else None,
+        "generate_s": gen_s,
+    }
+
+
+def run_batched_main(args):
+    """--workload msbm_batch256: the batched solve alone (one launch per step), e.g. for profiling."""
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_2210_16435_gb300 import buildlib
+
+    buildlib.build()
+    peak, _ = measured_peaks()
+    r = batched_extra(torch.device("cuda", 0), peak, scale=args.scale, sequential=not args.no_extras)
+    print(json.dumps({"metric": "batched k-eigenpair solve (256 graphs, one launch)", "value": r["solve_s"],
+                      "unit": "s/batch", "higher_is_better": False, "batched": r}), flush=True)
 
 
 # ---------------------------------------------------------------- oracle on the host cores
@@ -304,7 +418,7 @@ def run_ours(args):
     op_avg_ms = sum(i["ms_operator"] for i in infos) / max(1, sum(i["n_operator"] for i in infos))
     orth_avg_ms = sum(i["ms_orth"] for i in infos) / max(1, sum(i["n_orth"] for i in infos))
     op_bytes = operator_bytes(g.n, g.nnz, s_v, s_x, b)
-    orth_b = orth_bytes(g.n, inf["orth_cols"], inf["n_orth"], s_x, b) / max(1, inf["n_orth"])
+    orth_b = orth_bytes(g.n, inf["orth_cols"], inf["n_orth"], inf["orth_sweeps"], s_x, b) / max(1, inf["n_orth"])
     peak, peak_kind = measured_peaks()
     op_gbs = op_bytes / (op_avg_ms * 1e6)
     orth_gbs = orth_b / (orth_avg_ms * 1e6)
@@ -384,6 +498,9 @@ def run_ours(args):
         h2d = 4 * (g.n + 1) + 4 * g.nnz + VDT_BYTES[c["value_dtype"]] * g.nnz + 4 * g.n
         d2h = 8 * k + 8 * g.n * k + 4 * g.n
         line["e2e"] = {"value": e2e, "unit": "s/solve", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        # batched form (256 graphs, one launch) against sequential single-graph solves
+        if not args.no_batched:
+            line["batched"] = batched_extra(dev, peak)
         # the CPU oracle on the host cores (bounded sample, scaled to seconds per solve)
         if world == 1:
             model = oracle_step_model(args.workload, k)
@@ -398,6 +515,9 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.workload == "msbm_batch256" and args.impl != "reference":
+        run_batched_main(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -341,6 +341,11 @@ SFAIRSC_API int sfairsc_batch_schedule(sfairsc_batch* batch, int32_t ctas_per_sm
  * or DEVICE_TIMEOUT if a bounded device wait gave up. */
 SFAIRSC_API int sfairsc_batch_solve(sfairsc_batch* batch, int32_t* status, sfairsc_batch_info* info);
 
+/* Per-graph results of the last sfairsc_batch_solve (host arrays of count
+ * entries, each nullable): thick restarts, operator applications (4 per block
+ * step) and max_i ||A x_i - lambda_i x_i|| / sigma. */
+SFAIRSC_API int sfairsc_batch_stats(const sfairsc_batch* batch, int32_t* restarts, int32_t* matvecs, double* resid);
+
 SFAIRSC_API int sfairsc_batch_destroy(sfairsc_batch* batch);
 
 /* create + solve + destroy in one call. */

@@ -116,11 +116,12 @@ def load(path: str | None = None):
     lib.sfairsc_batch_schedule.argtypes = [vp, i32, i32, dbl]
     lib.sfairsc_batch_solve.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(BatchInfo)]
     lib.sfairsc_batch_destroy.argtypes = [vp]
+    lib.sfairsc_batch_stats.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(dbl)]
     lib.sfairsc_solve_batched.argtypes = [i32, ctypes.POINTER(BatchGraph), ctypes.POINTER(Opts),
                                           ctypes.POINTER(i32), ctypes.POINTER(BatchInfo), vp]
     for f in ("sfairsc_opts_default", "sfairsc_create", "sfairsc_destroy", "sfairsc_get_sigma",
               "sfairsc_apply_operator", "sfairsc_solve", "sfairsc_kmeans", "sfairsc_backward",
-              "sfairsc_batch_create", "sfairsc_batch_autotune", "sfairsc_batch_schedule", "sfairsc_batch_solve", "sfairsc_batch_destroy",
+              "sfairsc_batch_create", "sfairsc_batch_autotune", "sfairsc_batch_schedule", "sfairsc_batch_solve", "sfairsc_batch_destroy", "sfairsc_batch_stats",
               "sfairsc_solve_batched"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
@@ -225,6 +226,15 @@ def sfairsc_batch_solve(batch, count: int, allow=(0,)):
     rc = load().sfairsc_batch_solve(batch, st, ctypes.byref(info))
     _check(rc, "sfairsc_batch_solve", ok=allow)
     return rc, list(st), info
+
+
+def sfairsc_batch_stats(batch, count: int):
+    """Per-graph (restarts, matvecs, residual / sigma) lists of the last solve."""
+    r = (ctypes.c_int32 * count)()
+    m = (ctypes.c_int32 * count)()
+    d = (ctypes.c_double * count)()
+    _check(load().sfairsc_batch_stats(batch, r, m, d), "sfairsc_batch_stats")
+    return list(r), list(m), list(d)
 
 
 def sfairsc_batch_destroy(batch) -> None:

@@ -2318,6 +2318,17 @@ SFAIRSC_API int sfairsc_batch_solve(sfairsc_batch* b, int32_t* status, sfairsc_b
   return g != SFAIRSC_OK ? g : rc;
 }
 
+SFAIRSC_API int sfairsc_batch_stats(const sfairsc_batch* b, int32_t* restarts, int32_t* matvecs, double* resid) {
+  if (!b) return SFAIRSC_ERR_INVALID_ARG;
+  const sfairsc::BatchPlan& B = *reinterpret_cast<const sfairsc::BatchPlan*>(b);
+  for (int i = 0; i < B.count; ++i) {
+    if (restarts) restarts[i] = B.hstats[i].restarts;
+    if (matvecs) matvecs[i] = B.hstats[i].matvecs;
+    if (resid) resid[i] = B.hstats[i].max_resid;
+  }
+  return SFAIRSC_OK;
+}
+
 SFAIRSC_API int sfairsc_batch_destroy(sfairsc_batch* b) {
   sfairsc::batch_destroy(reinterpret_cast<sfairsc::BatchPlan*>(b));
   return SFAIRSC_OK;

@@ -177,6 +177,10 @@ class FairSCBatch:
         _, status, info = B.sfairsc_batch_solve(self.handle, self.count, allow=allow)
         return status, info.as_dict()
 
+    def stats(self):
+        """Per-graph restarts, matvecs and residuals of the last solve."""
+        return B.sfairsc_batch_stats(self.handle, self.count)
+
     def close(self):
         if getattr(self, "handle", None):
             B.sfairsc_batch_destroy(self.handle)
