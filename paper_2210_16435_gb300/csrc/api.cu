@@ -298,6 +298,7 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
     c->sigma = c->opts.sigma;
   }
   P[kPSigma] = c->sigma;
+  for (int a = 0; a + 1 < h; ++a) P[kPLinv + a] = 1.0 / P[kPL + a * kLStride + a];
   c->params = c->dalloc<double>(kParams);
   check_cuda(cudaMemcpyAsync(c->params, P, sizeof(double) * kParams, cudaMemcpyHostToDevice, s), "h2d");
 
@@ -329,11 +330,11 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   c->ytil = c->dalloc<unsigned char>((size_t)n * 4 * vs);
   c->ytil64 = c->dalloc<double>((size_t)n * 4);
   c->op_partial = c->dalloc<double>((size_t)grid * kMaxGroups * 4);
-  c->barrier = c->dalloc<unsigned>(4);
+  c->barrier = c->dalloc<unsigned>(8);
   c->err = c->barrier + 2;
   c->brk_step = c->dalloc<int>(1);
   c->sweeps = c->dalloc<int>(1);
-  check_cuda(cudaMemsetAsync(c->barrier, 0, 4 * sizeof(unsigned), s), "memset");
+  check_cuda(cudaMemsetAsync(c->barrier, 0, 8 * sizeof(unsigned), s), "memset");
   OpPlan& o = c->op;
   o.n = n;
   o.h = h;
@@ -341,10 +342,12 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   o.grid = grid;
   o.threads = threads;
   o.batch_rows = batch_rows;
-  {
-    const double avg = (double)c->nnz / std::max(n, 1);
-    o.lanes_per_row = std::min(32, std::max(4, next_pow2((int)std::ceil(avg / 4.0))));
-  }
+  // lanes per row of the SpMV: each lane holds 8 (FP32) or 4 (FP64) entries of its row per pass
+  const double avg_deg = (double)c->nnz / std::max(n, 1);
+  auto lanes_for = [&](double per_lane) {
+    return std::min(32, std::max(2, next_pow2((int)std::ceil(avg_deg / per_lane))));
+  };
+  o.lanes_per_row = lanes_for(c->vt == VecType::F64 ? 4.0 : 8.0);
   o.row_ptr = c->row_ptr;
   o.col = c->col;
   o.val = c->val;
@@ -358,11 +361,13 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   o.cta_rows = c->cta_rows;
   o.barrier = c->barrier;
   o.err = c->err;
+  o.work = c->barrier + 4;
   c->op64 = o;
   c->op64.val = c->val_orig;
   c->op64.val_dtype = c->vdt_orig;
   c->op64.dinv = c->dinv64;
   c->op64.ytil = c->ytil64;
+  c->op64.lanes_per_row = lanes_for(4.0);
   c->proj64 = c->op64;
   c->proj64.mode = 1;
 

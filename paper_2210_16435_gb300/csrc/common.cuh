@@ -19,12 +19,17 @@ enum : unsigned {
 };
 
 // ---------------------------------------------------------------- load helpers
+// A BF16 value is the upper half of the FP32 with the same sign, exponent and
+// leading mantissa bits, so widening is an exact 16-bit shift (integer pipe).
+__device__ __forceinline__ float bf16_bits_to_f32(__nv_bfloat16 v) {
+  return __uint_as_float(((unsigned)__bfloat16_as_ushort(v)) << 16);
+}
 __device__ __forceinline__ double to_f64(double v) { return v; }
 __device__ __forceinline__ double to_f64(float v) { return (double)v; }
-__device__ __forceinline__ double to_f64(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+__device__ __forceinline__ double to_f64(__nv_bfloat16 v) { return (double)bf16_bits_to_f32(v); }
 __device__ __forceinline__ float to_f32(double v) { return (float)v; }
 __device__ __forceinline__ float to_f32(float v) { return v; }
-__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return bf16_bits_to_f32(v); }
 
 template <typename VT>
 __device__ __forceinline__ VT cvt(double v);
@@ -40,13 +45,13 @@ __device__ __forceinline__ double val_as<double, double>(double v) { return v; }
 template <>
 __device__ __forceinline__ double val_as<double, float>(float v) { return (double)v; }
 template <>
-__device__ __forceinline__ double val_as<double, __nv_bfloat16>(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+__device__ __forceinline__ double val_as<double, __nv_bfloat16>(__nv_bfloat16 v) { return (double)bf16_bits_to_f32(v); }
 template <>
 __device__ __forceinline__ float val_as<float, double>(double v) { return (float)v; }
 template <>
 __device__ __forceinline__ float val_as<float, float>(float v) { return v; }
 template <>
-__device__ __forceinline__ float val_as<float, __nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float val_as<float, __nv_bfloat16>(__nv_bfloat16 v) { return bf16_bits_to_f32(v); }
 
 // ---------------------------------------------------------------- warp sums
 template <typename T>
@@ -86,6 +91,32 @@ struct Dot2 {
     two_sum(s, p, t, e);
     s = t;
     c = __fadd_rn(c, __fadd_rn(pe, e));
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// FP32 running sum with a TwoSum carry: s + c carries about twice FP32 precision.
+struct Comp32 {
+  float s, c;
+  __device__ __forceinline__ void zero() {
+    s = 0.f;
+    c = 0.f;
+  }
+  __device__ __forceinline__ void add(float x) {
+    float t, e;
+    two_sum(s, x, t, e);
+    s = t;
+    c = __fadd_rn(c, e);
+  }
+  // sum over lanes whose ids differ in bits >= from
+  __device__ __forceinline__ void reduce(int from) {
+    for (int o = from; o < 32; o <<= 1) {
+      const float os = __shfl_xor_sync(0xffffffffu, s, o), oc = __shfl_xor_sync(0xffffffffu, c, o);
+      float t, e;
+      two_sum(s, os, t, e);
+      s = t;
+      c = __fadd_rn(__fadd_rn(c, oc), e);
+    }
   }
   __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };

@@ -17,7 +17,8 @@ constexpr int kPZ = 0;                 // z_s = |V_s| / n, s < 32
 constexpr int kPL = 32;                // lower Cholesky factor of C^T C, row-major, stride 31
 constexpr int kLStride = 31;
 constexpr int kPSigma = kPL + 31 * 31; // sigma
-constexpr int kParams = 1024;
+constexpr int kPLinv = kPSigma + 1;    // reciprocals of the factor's diagonal, 31 entries
+constexpr int kParams = 1056;
 
 enum class VecType { F64 = 0, F32 = 1 };
 
@@ -48,8 +49,8 @@ struct OpPlan {
   int normalized = 1;
   int grid = 0;          // cooperative CTAs
   int threads = 1024;
-  int batch_rows = 32;   // rows per warp batch in the SpMV sweep (1..32)
-  int lanes_per_row = 8; // FP64 vectors: lanes per row (power of two, 4..32)
+  int batch_rows = 32;   // unused (kept for the plan layout)
+  int lanes_per_row = 8; // SpMV lanes per row (power of two, 2..32): 8 FP32 / 4 FP64 entries per lane per pass
   int mode = 0;          // 0: L_n^sigma w, 1: P w
   const int32_t* row_ptr = nullptr;
   const int32_t* col = nullptr;
@@ -64,6 +65,7 @@ struct OpPlan {
   const int32_t* cta_rows = nullptr;  // int32[grid + 1]
   unsigned* barrier = nullptr; // 2 words
   unsigned* err = nullptr;
+  unsigned* work = nullptr;    // 1 word: dynamic row-block counter of the SpMV
 };
 
 // Launch out = L_n^sigma w for nvec vectors; element (r, v) of w is w[r*wrs + v*wcs]
@@ -92,7 +94,7 @@ struct OrthPlan {
   int grid = 0;
   int threads = 1024;
   int64_t ldv = 0;
-  void* V = nullptr;          // VT, n x ldv columns
+  void* V = nullptr;          // VT, ldv/4 panels of 4 columns, each n x 4 row-major
   void* U = nullptr;          // VT, n x 4 row-major: the block being orthogonalised
   void* Q = nullptr;          // VT, n x 4 row-major: copy of the newest basis block (operator input)
   double* H = nullptr;        // projected matrix, column-major, ld ldh
@@ -111,6 +113,7 @@ struct OrthPlan {
 void launch_orth(const OrthPlan& p, VecType vt, int J, int j, int B, cudaStream_t s);
 int orth_max_grid(VecType vt, int B, int threads);
 // V[:, 0:K] = V[:, 0:m] Y (Y: m x K column-major FP64 on device), then V[:, K:K+B] = V[:, m:m+B].
+// V is stored as ldv/4 panels of n x 4 (panel p = columns 4p..4p+3).
 // Q (n x 4 row-major) receives the carried block too.
 void launch_restart(VecType vt, int n, void* V, int64_t ldv, int m, int K, int B, const double* Y, void* Q,
                     cudaStream_t s);

@@ -2,21 +2,20 @@
 // CGS2 orthogonalisation of a new block against the basis, Cholesky-QR of the
 // block, thick restart V <- V Y, and the final FP64 checks / embedding.
 //
-// The basis V is ROW-major (n x ldv): a warp reads one row of up to 256
-// basis coefficients as 32-lane coalesced lines, each lane owning a column.
-// Inner products V^T u accumulate in FP64 (FP64 path) or in compensated
-// FP32 pairs (Dot2, mixed path), and are reduced across CTAs in a fixed
-// order, so every run is bitwise reproducible.
+// The basis V is stored as ldv/4 panels of 4 columns, each an n x 4
+// row-major array (panel p = columns 4p..4p+3), so a run of rows of one
+// panel is contiguous.
 #include "common.cuh"
 #include "internal.h"
 
 namespace sfairsc {
 
 // ---------------------------------------------------------------- thick restart / Ritz vectors
-// OUT[r, 0:K] = V[r, 0:m] Y[:, 0:K] for a 64-row tile: the tile of V is held
-// transposed in shared memory (stride 68), Y in 64-column chunks, and each of
-// the 256 threads accumulates a 4 x 4 block (rows 4*tr.., columns 4*tc..)
-// from two 16-byte shared loads per inner step.
+// OUT[r, 0:K] = V[r, 0:m] Y[:, 0:K] for a 64-row tile: the tile of V (read
+// panel by panel, 1 KB contiguous per panel) is held transposed in shared
+// memory (stride 68), Y in 64-column chunks, and each of the 256 threads
+// accumulates a 4 x 4 block (rows 4*tr.., columns 4*tc..) from two 16-byte
+// shared loads per inner step.
 constexpr int kTR = 64;       // rows per CTA
 constexpr int kTS = kTR + 4;  // transposed stride (keeps 16-byte alignment)
 
@@ -44,9 +43,11 @@ __global__ void __launch_bounds__(256) tile_gemm_kernel(int n, VT* V, int64_t ld
   const int t = threadIdx.x, tr = t >> 4, tc = t & 15;
   const int rbase = blockIdx.x * kTR;
   const int rows = min(kTR, n - rbase);
-  for (int i = t; i < kTR * width; i += blockDim.x) {
-    const int rr = i / width, c = i % width;
-    Vt[(size_t)c * kTS + rr] = rr < rows ? V[(size_t)(rbase + rr) * ldv + c] : VT(0);
+  const size_t pn = (size_t)n * 4;
+  const int width4 = (width + 3) & ~3;
+  for (int i = t; i < kTR * width4; i += blockDim.x) {
+    const int p = i / (kTR * 4), rem = i % (kTR * 4), rr = rem >> 2, c = 4 * p + (rem & 3);
+    if (c < width) Vt[(size_t)c * kTS + rr] = rr < rows ? V[p * pn + (size_t)(rbase + rr) * 4 + (rem & 3)] : VT(0);
   }
   for (int k0 = 0; k0 < K; k0 += 64) {
     const int kc = min(64, K - k0);
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(256) tile_gemm_kernel(int n, VT* V, int64_t ld
       for (int j = 0; j < 4; ++j) {
         const int col = 4 * tc + j;
         if (col < kc) {
-          if (MODE == 0) V[(size_t)r * ldv + k0 + col] = acc[i][j];
+          if (MODE == 0) V[((k0 + col) >> 2) * pn + (size_t)r * 4 + ((k0 + col) & 3)] = acc[i][j];
           else X[(size_t)r + (size_t)(k0 + col) * n] = (double)acc[i][j];
         }
       }
@@ -90,7 +91,7 @@ __global__ void __launch_bounds__(256) tile_gemm_kernel(int n, VT* V, int64_t ld
     for (int i = t; i < rows * B; i += blockDim.x) {
       const int rr = i / B, v = i % B;
       const VT x = Vt[(size_t)(m + v) * kTS + rr];
-      V[(size_t)(rbase + rr) * ldv + K + v] = x;
+      V[((K + v) >> 2) * pn + (size_t)(rbase + rr) * 4 + ((K + v) & 3)] = x;
       Q[(size_t)(rbase + rr) * 4 + v] = x;
     }
   }
@@ -178,7 +179,7 @@ template <typename VT>
 __global__ void to_f64_kernel(int n, const VT* V, int64_t ldv, int k, double* X) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
-  for (int c = 0; c < k; ++c) X[(size_t)r + (size_t)c * n] = (double)V[(size_t)r * ldv + c];
+  for (int c = 0; c < k; ++c) X[(size_t)r + (size_t)c * n] = (double)V[(size_t)(c >> 2) * n * 4 + (size_t)r * 4 + (c & 3)];
 }
 
 void launch_to_f64(VecType vt, int n, const void* V, int64_t ldv, int k, double* X, cudaStream_t s) {

@@ -43,7 +43,34 @@ struct OpArgs {
   const int32_t* __restrict__ cta_rows;
   GridBarrier bar;
   unsigned* err;
+  unsigned* work;  // dynamic row-block counter of the SpMV phase
 };
+
+template <typename VT, int B>
+__device__ __forceinline__ void load_row(const VT* p, VT (&x)[B]);
+
+// B contiguous values through L2 (data written by other CTAs in this launch).
+template <typename VT, int B>
+__device__ __forceinline__ void load_row_cg(const VT* p, VT (&x)[B]) {
+  if constexpr (sizeof(VT) == 4 && B == 4) {
+    const float4 v = __ldcg(reinterpret_cast<const float4*>(p));
+    x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+  } else {
+#pragma unroll
+    for (int v = 0; v < B; ++v) x[v] = __ldcg(p + v);
+  }
+}
+
+// Element v of row r of a strided n x B block (rs, cs): one vector load when the rows are contiguous.
+template <typename VT, int B>
+__device__ __forceinline__ void load_strided(const VT* base, int64_t r, int64_t rs, int64_t cs, VT (&x)[B]) {
+  if (cs == 1 && rs == B) {
+    load_row<VT, B>(base + r * B, x);
+  } else {
+#pragma unroll
+    for (int v = 0; v < B; ++v) x[v] = base[r * rs + v * cs];
+  }
+}
 
 template <typename VT, int B>
 __device__ __forceinline__ void load_row(const VT* p, VT (&x)[B]) {
@@ -66,43 +93,6 @@ __device__ __forceinline__ void load_row(const VT* p, VT (&x)[B]) {
   }
 }
 
-// Adds x (one value per vector, per lane) into lane s's accumulators for the
-// lanes whose label is s.  All 32 lanes must call it.  The warp sums run in
-// the vector precision (FP64 arithmetic is 1/58 of FP32 on this part); the
-// per-lane running sums are carried into FP64 by the caller.
-template <int B, typename VT>
-__device__ __forceinline__ void warp_group_add(const VT (&x)[B], int label, bool valid, int h, VT (&acc)[B]) {
-  const int lane = threadIdx.x & 31;
-  for (int s = 0; s < h; ++s) {
-    const bool mine = valid && label == s;
-    if (__ballot_sync(0xffffffffu, mine) == 0u) continue;
-#pragma unroll
-    for (int v = 0; v < B; ++v) {
-      const VT t = warp_allsum(mine ? x[v] : VT(0));
-      if (lane == s) acc[v] += t;
-    }
-  }
-}
-
-// Block reduction of the per-warp group accumulators (lane s holds group s)
-// into partial[blockIdx.x][s * B + v], in a fixed warp order.
-template <int B>
-__device__ __forceinline__ void block_group_store(const double (&acc)[B], int h, double* red, double* partial) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const int P = h * B;
-  if (lane < h) {
-#pragma unroll
-    for (int v = 0; v < B; ++v) red[warp * P + lane * B + v] = acc[v];
-  }
-  __syncthreads();
-  for (int p = threadIdx.x; p < P; p += blockDim.x) {
-    double s = 0.0;
-    for (int wv = 0; wv < nwarps; ++wv) s += red[wv * P + p];
-    partial[(size_t)blockIdx.x * P + p] = s;
-  }
-  __syncthreads();
-}
-
 // Sum partial[cta][p] over all CTAs in a fixed order into out[p] (shared).
 __device__ __forceinline__ void reduce_partials(const double* partial, int nctas, int P, double* scratch, double* out) {
   const int T = blockDim.x;
@@ -112,7 +102,16 @@ __device__ __forceinline__ void reduce_partials(const double* partial, int nctas
   if (c < nchunk) {
     const int lo = (int)((long long)c * nctas / nchunk), hi = (int)((long long)(c + 1) * nctas / nchunk);
     double s = 0.0;
-    for (int i = lo; i < hi; ++i) s += __ldcg(partial + (size_t)i * P + p);
+    int i = lo;
+    for (; i + 4 <= hi; i += 4) {  // four loads in flight, added in order
+      const double x0 = __ldcg(partial + (size_t)i * P + p), x1 = __ldcg(partial + (size_t)(i + 1) * P + p);
+      const double x2 = __ldcg(partial + (size_t)(i + 2) * P + p), x3 = __ldcg(partial + (size_t)(i + 3) * P + p);
+      s += x0;
+      s += x1;
+      s += x2;
+      s += x3;
+    }
+    for (; i < hi; ++i) s += __ldcg(partial + (size_t)i * P + p);
     scratch[c * P + p] = s;
   }
   __syncthreads();
@@ -141,13 +140,13 @@ __device__ __forceinline__ void solve_groups(const double* tot, const double* pa
     for (int s = 0; s < p; ++s) {
       double r = tot[s * B + v] - params[kPZ + s] * sum;
       for (int q = 0; q < s; ++q) r -= params[kPL + s * kLStride + q] * y[q];
-      y[s] = r / params[kPL + s * kLStride + s];
+      y[s] = r * params[kPLinv + s];
     }
     // backward: L^T a = y
     for (int s = p - 1; s >= 0; --s) {
       double r = y[s];
       for (int q = s + 1; q < p; ++q) r -= params[kPL + q * kLStride + s] * y[q];
-      y[s] = r / params[kPL + s * kLStride + s];
+      y[s] = r * params[kPLinv + s];
     }
     double za = 0.0;
     for (int s = 0; s < p; ++s) za += params[kPZ + s] * y[s];
@@ -160,6 +159,108 @@ __device__ __forceinline__ void solve_groups(const double* tot, const double* pa
   __syncthreads();
 }
 
+// Group sums of f(r) (B values per row) over rows [r0, r1) of this CTA:
+// partial[blockIdx.x][s * B + v] = sum over own rows i in V_s of f(i)_v.
+// Thread per row; groups are taken 4 per pass with predicated adds (no
+// per-row shuffles).  FP32: per-thread windows of 16 rows carried by TwoSum,
+// combined over the warp by a TwoSum tree; FP64: FP64 throughout.  Warps are
+// then added in a fixed order, so the result is bitwise reproducible.
+template <typename VT, int B, typename F>
+__device__ void cta_group_sums(int r0, int r1, int h, const uint8_t* __restrict__ lab, double* red, double* partial,
+                               F&& f) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int P = h * B;
+  for (int s0 = 0; s0 < h; s0 += 4) {
+    if constexpr (sizeof(VT) == 4) {
+      float win[4][B];
+      Comp32 acc[4][B];
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int v = 0; v < B; ++v) {
+          win[j][v] = 0.f;
+          acc[j][v].zero();
+        }
+      int cnt = 0;
+      const int T = blockDim.x;
+      for (int r = r0 + threadIdx.x; r < r1; r += 4 * T) {
+        // four rows' loads in flight before their adds
+        int g[4];
+        float x[4][B];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {  // loads are not predicated on the label (one round trip)
+          const int rk = r + k * T;
+          g[k] = rk < r1 ? (int)lab[rk] - s0 : -1;
+          if (rk < r1) f(rk, x[k]);
+          else
+#pragma unroll
+            for (int v = 0; v < B; ++v) x[k][v] = 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int v = 0; v < B; ++v) win[j][v] += g[k] == j ? x[k][v] : 0.f;
+        if (++cnt == 4) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int v = 0; v < B; ++v) {
+              acc[j][v].add(win[j][v]);
+              win[j][v] = 0.f;
+            }
+          cnt = 0;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int v = 0; v < B; ++v) {
+          acc[j][v].add(win[j][v]);
+          acc[j][v].reduce(1);
+        }
+      if (lane == 0)
+        for (int j = 0; j < 4 && s0 + j < h; ++j)
+#pragma unroll
+          for (int v = 0; v < B; ++v) red[warp * P + (s0 + j) * B + v] = acc[j][v].value();
+    } else {
+      double acc[4][B];
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int v = 0; v < B; ++v) acc[j][v] = 0.0;
+      for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        const int g = (int)lab[r] - s0;
+        if (g >= 0 && g < 4) {
+          double x[B];
+          f(r, x);
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (g == j)
+#pragma unroll
+              for (int v = 0; v < B; ++v) acc[j][v] += x[v];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int v = 0; v < B; ++v) acc[j][v] = warp_allsum(acc[j][v]);
+      if (lane == 0)
+        for (int j = 0; j < 4 && s0 + j < h; ++j)
+#pragma unroll
+          for (int v = 0; v < B; ++v) red[warp * P + (s0 + j) * B + v] = acc[j][v];
+    }
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    double s = 0.0;
+    for (int wv = 0; wv < nwarps; ++wv) s += red[wv * P + p];
+    partial[(size_t)blockIdx.x * P + p] = s;
+  }
+  __syncthreads();
+}
+
 template <typename VT, typename MT, int B>
 __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -168,14 +269,13 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
   const int P = h * B;
   const bool grouped = h > 1;
   // shared layout
-  VT* rows_s = reinterpret_cast<VT*>(smem_raw);                                     // nwarps * 32 * B
-  double* red = reinterpret_cast<double*>(smem_raw + sizeof(VT) * nwarps * 32 * B);  // nwarps * P
-  double* scratch = red + nwarps * P;                                                // blockDim.x (+P)
-  double* tot = scratch + blockDim.x + P;                                            // P
-  double* avec = tot + kMaxGroups * B;                                               // 32*B
-  double* coefA = avec + kMaxGroups * B;                                             // 32*B
-  double* coefD = coefA + kMaxGroups * B;                                            // 32*B
-  int* rp_s = reinterpret_cast<int*>(coefD + kMaxGroups * B);                         // nwarps * 33
+  double* red = reinterpret_cast<double*>(smem_raw);  // nwarps * P
+  double* scratch = red + nwarps * P;                  // blockDim.x (+P)
+  double* tot = scratch + blockDim.x + P;              // P
+  double* avec = tot + kMaxGroups * B;                 // 32*B
+  double* coefA = avec + kMaxGroups * B;               // 32*B
+  double* coefD = coefA + kMaxGroups * B;              // 32*B
+  VT* coefAv = reinterpret_cast<VT*>(coefD + kMaxGroups * B);  // 32*B, in the vector type
 
   const int r0 = a.cta_rows[blockIdx.x], r1 = a.cta_rows[blockIdx.x + 1];
 
@@ -183,41 +283,12 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
 
   // ---------------- phase A: group sums of D^{-1/2} w over own rows
   if (grouped) {
-    double acc[B];
-    VT accw[B];
+    cta_group_sums<VT, B>(r0, r1, h, a.lab, red, a.partial, [&](int r, VT(&x)[B]) {
+      const VT sc = scale(r);
+      load_strided<VT, B>(a.w, r, a.wrs, a.wcs, x);
 #pragma unroll
-    for (int v = 0; v < B; ++v) {
-      acc[v] = 0.0;
-      accw[v] = VT(0);
-    }
-    int nb = 0;
-    for (int base = r0 + warp * 32; base < r1; base += nwarps * 32) {
-      const int r = base + lane;
-      const bool valid = r < r1;
-      VT x[B];
-      int g = 0;
-      if (valid) {
-        g = a.lab[r];
-        const VT sc = scale(r);
-#pragma unroll
-        for (int v = 0; v < B; ++v) x[v] = a.w[r * a.wrs + v * a.wcs] * sc;
-      } else {
-#pragma unroll
-        for (int v = 0; v < B; ++v) x[v] = VT(0);
-      }
-      warp_group_add<B>(x, g, valid, h, accw);
-      if (++nb == 8) {
-#pragma unroll
-        for (int v = 0; v < B; ++v) {
-          acc[v] += (double)accw[v];
-          accw[v] = VT(0);
-        }
-        nb = 0;
-      }
-    }
-#pragma unroll
-    for (int v = 0; v < B; ++v) acc[v] += (double)accw[v];
-    block_group_store<B>(acc, h, red, a.partial);
+      for (int v = 0; v < B; ++v) x[v] *= sc;
+    });
     if (!grid_sync(a.bar, a.err)) return;
     // ---------------- phase B: a = (C^T C)^{-1} C^T w
     reduce_partials(a.partial, gridDim.x, P, scratch, tot);
@@ -229,12 +300,14 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
     }
     __syncthreads();
   }
+  for (int i = threadIdx.x; i < kMaxGroups * B; i += blockDim.x) coefAv[i] = (VT)coefA[i];
+  __syncthreads();
   if (a.mode == 1) {  // P w only
     for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
       const int g = a.lab[r];
       const VT sc = scale(r);
 #pragma unroll
-      for (int v = 0; v < B; ++v) a.out[r * a.ors + v * a.ocs] = a.w[r * a.wrs + v * a.wcs] - sc * (VT)coefA[g * B + v];
+      for (int v = 0; v < B; ++v) a.out[r * a.ors + v * a.ocs] = a.w[r * a.wrs + v * a.wcs] - sc * coefAv[g * B + v];
     }
     return;
   }
@@ -244,168 +317,149 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
     const VT sc = scale(r);
 #pragma unroll
     for (int v = 0; v < B; ++v) {
-      const VT y = a.w[r * a.wrs + v * a.wcs] - sc * (VT)coefA[g * B + v];
+      const VT y = a.w[r * a.wrs + v * a.wcs] - sc * coefAv[g * B + v];
       a.ytil[(size_t)r * B + v] = a.normalized ? sc * y : y;
     }
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.work = 0u;  // no CTA takes a block before the barrier
   if (!grid_sync(a.bar, a.err)) return;
 
-  // ---------------- phase C: t = L_n y, written to out; group sums of D^{-1/2} t
-  // Each warp sweeps the stored entries of a 32-row batch as one flat,
-  // coalesced stream (entry e0 + 32u + lane), gathers ytil, and sums the
-  // products per row with a segmented warp scan; the tail lane of every row
-  // segment adds it to that row's shared-memory sum.  The summation tree is
-  // fixed, so results are bitwise reproducible.
-  double acc[B];
-  VT accw[B];
+  // ---------------- phase C: t = L_n y, written to out
+  // Warps take blocks of 4 row groups from a global counter (load balance
+  // across CTAs); Lr lanes per row, each holding up to U (column, weight)
+  // pairs of its row per pass; within a block the pairs of the next row group
+  // and the bounds of the group after it are loaded while this group's ytil
+  // rows are gathered.  Sums per row by a fixed shuffle tree (reproducible).
+  {
+    constexpr int U = sizeof(VT) == 4 ? 8 : 4;
+    constexpr int kGroupsPerBlock = 4;
+    const int Lr = a.lanes;
+    const int sub = lane & (Lr - 1);
+    const int rpw = 32 / Lr;
+    const int n = a.n;
+    auto bounds = [&](int rb, int rend, int& e, int& e1) {
+      const int r = rb + lane / Lr;
+      if (r < rend) {
+        e = __ldg(a.row_ptr + r) + sub;
+        e1 = __ldg(a.row_ptr + r + 1);
+      } else {
+        e = 0;
+        e1 = 0;
+      }
+    };
+    auto fetch = [&](int e, int e1, int (&c)[U], VT (&wv)[U]) {
 #pragma unroll
-  for (int v = 0; v < B; ++v) {
-    acc[v] = 0.0;
-    accw[v] = VT(0);
-  }
-  int nbc = 0;
-  VT* myrows = rows_s + warp * 32 * B;
-  int* rps = rp_s + warp * 33;
-  constexpr int UCH = B >= 4 ? 2 : 4;  // 32-entry chunks per stage
-  const int RB = a.batch_rows;          // rows per warp batch (1..32)
-  for (int base = r0 + warp * RB; base < r1; base += nwarps * RB) {
-    const int nr = min(RB, r1 - base);
-    if (lane < nr) rps[lane] = __ldg(a.row_ptr + base + lane);
-    if (lane == 0) rps[nr] = __ldg(a.row_ptr + base + nr);
+      for (int u = 0; u < U; ++u) {
+        const int ee = e + u * Lr;
+        const bool in = ee < e1;
+        c[u] = in ? __ldg(a.col + ee) : -1;
+        wv[u] = in ? val_as<VT>(a.val[ee]) : VT(0);
+      }
+    };
+    const int blk_rows = rpw * kGroupsPerBlock;
+    const int nblocks = (n + blk_rows - 1) / blk_rows;
+    auto grab = [&]() {
+      int b = 0;
+      if (lane == 0) b = (int)atomicAdd(a.work, 1u);
+      return __shfl_sync(0xffffffffu, b, 0);
+    };
+    // look-ahead iterator over the row groups of the blocks this warp takes
+    // (row base n = exhausted); the block after the current one is taken early
+    int la_blk = grab(), la_next = grab();
+    int la_rb = la_blk < nblocks ? la_blk * blk_rows : n;
+    auto advance = [&]() {
+      if (la_rb >= n) return;
+      la_rb += rpw;
+      if (la_rb >= min(n, la_blk * blk_rows + blk_rows)) {
+        la_blk = la_next;
+        la_rb = la_blk < nblocks ? la_blk * blk_rows : n;
+        if (la_blk < nblocks) la_next = grab();
+      }
+    };
+    auto rend_of = [&](int rb) { return min(n, (rb / blk_rows) * blk_rows + blk_rows); };
+    int rb_cur = la_rb;
+    advance();
+    int rb_nx = la_rb;
+    advance();
+    int e_cur, e1_cur, e_nx, e1_nx;
+    int c_cur[U];
+    VT w_cur[U];
+    bounds(rb_cur, rb_cur < n ? rend_of(rb_cur) : n, e_cur, e1_cur);
+    fetch(e_cur, e1_cur, c_cur, w_cur);
+    bounds(rb_nx, rb_nx < n ? rend_of(rb_nx) : n, e_nx, e1_nx);
+    while (rb_cur < n) {
+      int c_nx[U];
+      VT w_nx[U];
+      fetch(e_nx, e1_nx, c_nx, w_nx);  // the next group's pairs, in flight during this group's gathers
+      const int rb_nn = la_rb;
+      advance();
+      int e_nn, e1_nn;
+      bounds(rb_nn, rb_nn < n ? rend_of(rb_nn) : n, e_nn, e1_nn);
+      const int rend = rend_of(rb_cur);
+      VT sacc[B];
 #pragma unroll
-    for (int v = 0; v < B; ++v) myrows[lane * B + v] = VT(0);
-    __syncwarp();
-    if constexpr (sizeof(VT) == 8) {
-      // FP64 vectors: L lanes per row, one FMA per entry and log2(L) shuffle
-      // levels per row (a flat scan would cost several FP64 adds per entry).
-      const int L = a.lanes, sub = lane & (L - 1), per = 32 / L;
-      for (int pass = 0; pass * per < nr; ++pass) {
-        const int rib = pass * per + lane / L;
-        VT sacc[B];
+      for (int v = 0; v < B; ++v) sacc[v] = VT(0);
 #pragma unroll
-        for (int v = 0; v < B; ++v) sacc[v] = VT(0);
-        if (rib < nr) {
-          int e = rps[rib] + sub;
-          const int e1 = rps[rib + 1];
-          for (; e + L < e1; e += 2 * L) {
-            const int c0 = __ldg(a.col + e), c1 = __ldg(a.col + e + L);
-            const VT w0 = val_as<VT>(a.val[e]), w1 = val_as<VT>(a.val[e + L]);
-            VT y0[B], y1[B];
-            load_row<VT, B>(a.ytil + (size_t)c0 * B, y0);
-            load_row<VT, B>(a.ytil + (size_t)c1 * B, y1);
+      for (int u = 0; u < U; ++u) {
+        if (c_cur[u] >= 0) {
+          VT y[B];
+          load_row<VT, B>(a.ytil + (size_t)c_cur[u] * B, y);
 #pragma unroll
-            for (int v = 0; v < B; ++v) sacc[v] = fma(w1, y1[v], fma(w0, y0[v], sacc[v]));
-          }
-          if (e < e1) {
-            const int c0 = __ldg(a.col + e);
-            const VT w0 = val_as<VT>(a.val[e]);
-            VT y0[B];
-            load_row<VT, B>(a.ytil + (size_t)c0 * B, y0);
-#pragma unroll
-            for (int v = 0; v < B; ++v) sacc[v] = fma(w0, y0[v], sacc[v]);
-          }
-        }
-        for (int o = L >> 1; o > 0; o >>= 1) {
-#pragma unroll
-          for (int v = 0; v < B; ++v) sacc[v] += __shfl_xor_sync(0xffffffffu, sacc[v], o);
-        }
-        if (sub == 0 && rib < nr) {
-#pragma unroll
-          for (int v = 0; v < B; ++v) myrows[rib * B + v] = sacc[v];
+          for (int v = 0; v < B; ++v) sacc[v] = fma(w_cur[u], y[v], sacc[v]);
         }
       }
-    } else {
-      const int E0 = rps[0], E1 = rps[nr];
-      int cur = 0;
-      int cc[UCH];
-      VT wv[UCH];
-      auto fetch = [&](int e0, int (&c)[UCH], VT (&w)[UCH]) {
-  #pragma unroll
-        for (int u = 0; u < UCH; ++u) {
-          const int e = e0 + 32 * u + lane;
-          const bool ok = e < E1;
-          c[u] = ok ? __ldg(a.col + e) : 0;
-          w[u] = ok ? val_as<VT>(a.val[e]) : VT(0);
-        }
-      };
-      fetch(E0, cc, wv);
-      for (int e0 = E0; e0 < E1; e0 += 32 * UCH) {
-        VT y[UCH][B];
-  #pragma unroll
-        for (int u = 0; u < UCH; ++u) load_row<VT, B>(a.ytil + (size_t)cc[u] * B, y[u]);
-        int ncc[UCH];
-        VT nwv[UCH];
-        fetch(e0 + 32 * UCH, ncc, nwv);  // next stage's indices and weights, in flight during this one
-  #pragma unroll
-        for (int u = 0; u < UCH; ++u) {
-          const int e = e0 + 32 * u + lane;
-          const bool ok = e < E1;
-          if (ok)
-            while (e >= rps[cur + 1]) ++cur;
-          const int rid = ok ? cur : 32;
-          VT p[B];
-  #pragma unroll
-          for (int v = 0; v < B; ++v) p[v] = wv[u] * y[u][v];
-  #pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const int ro = __shfl_up_sync(0xffffffffu, rid, o);
-  #pragma unroll
-            for (int v = 0; v < B; ++v) {
-              const VT t = __shfl_up_sync(0xffffffffu, p[v], o);
-              if (lane >= o && ro == rid) p[v] += t;
-            }
-          }
-          const int rn = __shfl_down_sync(0xffffffffu, rid, 1);
-          if (ok && (lane == 31 || rn != rid)) {
-  #pragma unroll
-            for (int v = 0; v < B; ++v) myrows[rid * B + v] += p[v];
-          }
-          __syncwarp();
-        }
-  #pragma unroll
-        for (int u = 0; u < UCH; ++u) {
-          cc[u] = ncc[u];
-          wv[u] = nwv[u];
-        }
-      }
-    }
-    __syncwarp();
-    const int r = base + lane;
-    const bool valid = lane < nr;
-    VT x[B];
-    int g = 0;
-    if (valid) {
-      g = a.lab[r];
-      const VT sc = scale(r);
-      const VT dd = a.normalized ? VT(1) : (VT)a.deg[r];
+      for (int e = e_cur + U * Lr; e < e1_cur; e += Lr) {  // rows longer than U * Lr entries
+        const int c = __ldg(a.col + e);
+        const VT w = val_as<VT>(a.val[e]);
+        VT y[B];
+        load_row<VT, B>(a.ytil + (size_t)c * B, y);
 #pragma unroll
-      for (int v = 0; v < B; ++v) {
-        const VT y = a.w[r * a.wrs + v * a.wcs] - sc * (VT)coefA[g * B + v];
-        const VT t = a.normalized ? y - sc * myrows[lane * B + v] : dd * y - myrows[lane * B + v];
-        a.out[r * a.ors + v * a.ocs] = t;
-        x[v] = sc * t;
+        for (int v = 0; v < B; ++v) sacc[v] = fma(w, y[v], sacc[v]);
       }
-    } else {
+      for (int o = Lr >> 1; o > 0; o >>= 1)
 #pragma unroll
-      for (int v = 0; v < B; ++v) x[v] = VT(0);
-    }
-    __syncwarp();
-    if (grouped) {
-      warp_group_add<B>(x, g, valid, h, accw);
-      if (++nbc == 8) {
+        for (int v = 0; v < B; ++v) sacc[v] += __shfl_xor_sync(0xffffffffu, sacc[v], o);
+      const int r = rb_cur + lane / Lr;
+      if (r < rend && sub == 0) {
+        const int g = a.lab[r];
+        const VT sc = scale(r);
+        VT dd = VT(1);
+        if (!a.normalized) dd = (VT)a.deg[r];
+        VT wr[B];
+        load_strided<VT, B>(a.w, r, a.wrs, a.wcs, wr);
 #pragma unroll
         for (int v = 0; v < B; ++v) {
-          acc[v] += (double)accw[v];
-          accw[v] = VT(0);
+          const VT y = wr[v] - sc * coefAv[g * B + v];
+          a.out[r * a.ors + v * a.ocs] = a.normalized ? y - sc * sacc[v] : dd * y - sacc[v];
         }
-        nbc = 0;
       }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        c_cur[u] = c_nx[u];
+        w_cur[u] = w_nx[u];
+      }
+      e_cur = e_nx;
+      e1_cur = e1_nx;
+      e_nx = e_nn;
+      e1_nx = e1_nn;
+      rb_cur = rb_nx;
+      rb_nx = rb_nn;
     }
   }
   if (!grouped) return;
+  // t rows were written by any CTA: make them visible, then group sums over own rows (through L2)
+  if (!grid_sync(a.bar, a.err)) return;
+  cta_group_sums<VT, B>(r0, r1, h, a.lab, red, a.partial, [&](int r, VT(&x)[B]) {
+    const VT sc = scale(r);
+    if (a.ocs == 1 && a.ors == B) {
+      load_row_cg<VT, B>(a.out + (size_t)r * B, x);
 #pragma unroll
-  for (int v = 0; v < B; ++v) acc[v] += (double)accw[v];
-  block_group_store<B>(acc, h, red, a.partial);
+      for (int v = 0; v < B; ++v) x[v] *= sc;
+    } else {
+#pragma unroll
+      for (int v = 0; v < B; ++v) x[v] = sc * __ldcg(a.out + r * a.ors + v * a.ocs);
+    }
+  });
   if (!grid_sync(a.bar, a.err)) return;
 
   // ---------------- phase D: b = (C^T C)^{-1} C^T t; out = t - C (b - sigma a)
@@ -428,13 +482,18 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
       coefD[p * B + v] = -zu;
     }
     __syncthreads();
+    for (int i = threadIdx.x; i < kMaxGroups * B; i += blockDim.x) coefAv[i] = (VT)coefD[i];
+    __syncthreads();
   }
 #pragma unroll 4
   for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
     const int g = a.lab[r];
     const VT sc = scale(r);
 #pragma unroll
-    for (int v = 0; v < B; ++v) a.out[r * a.ors + v * a.ocs] -= sc * (VT)coefD[g * B + v];
+    for (int v = 0; v < B; ++v) {
+      VT* o = a.out + r * a.ors + v * a.ocs;
+      *o = __ldcg(o) - sc * coefAv[g * B + v];
+    }
   }
 }
 
@@ -442,8 +501,7 @@ size_t operator_smem_bytes(int threads, int h, int nvec, VecType vt) {
   const int nwarps = threads / 32;
   const size_t vs = vt == VecType::F64 ? 8 : 4;
   const int P = h * nvec;
-  return vs * nwarps * 32 * nvec + sizeof(double) * ((size_t)nwarps * P + threads + P + 4 * kMaxGroups * nvec) +
-         sizeof(int) * nwarps * 33 + 64;
+  return sizeof(double) * ((size_t)nwarps * P + threads + P + 4 * kMaxGroups * nvec) + vs * kMaxGroups * nvec + 64;
 }
 
 template <typename VT, typename MT, int B>
@@ -474,6 +532,7 @@ static void launch_t(const OpPlan& p, const void* w, int64_t wrs, int64_t wcs, v
   a.cta_rows = p.cta_rows;
   a.bar = GridBarrier{p.barrier, p.barrier + 1};
   a.err = p.err;
+  a.work = p.work;
   const size_t smem = operator_smem_bytes(p.threads, p.h, B, sizeof(VT) == 8 ? VecType::F64 : VecType::F32);
   auto kern = fused_operator_kernel<VT, MT, B>;
   check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "operator smem attr");
@@ -534,7 +593,7 @@ static int max_grid_t(int threads, size_t smem) {
 }
 
 int operator_max_grid(VecType vt, int val_dtype, int nvec, int threads, size_t smem) {
-  // Occupancy is limited by the 1024-thread CTA; every instantiation fits one CTA per SM.
+  // One CTA per SM (cooperative grid); the smallest co-resident grid over the instantiations.
   int best = 1 << 30;
   auto upd = [&](int g) { best = g < best ? g : best; };
   if (vt == VecType::F64) {

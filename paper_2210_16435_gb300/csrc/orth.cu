@@ -9,82 +9,98 @@
 // sweep applies the second projection only when some column kept less than
 // 1/sqrt(2) of its norm.  So a launch reads V twice, or three times.
 //
-// One cooperative launch; each CTA owns a contiguous row range of the
-// ROW-major basis (n x ldv).  Rows stream through a ring of shared-memory
-// stages filled by the bulk-copy (TMA) engine (cp.async.bulk + mbarrier),
-// so the bytes in flight do not occupy registers.  Lane l of a warp owns
-// columns 4l..4l+3 (+128 per chunk).  Inner products accumulate per lane in
-// FP32 over windows of 32 rows and are carried in FP64 per warp, then summed
-// over warps and CTAs in a fixed order (bitwise reproducible); the FP64
-// path accumulates in FP64 throughout.  Every mbarrier wait is bounded.
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
+// One cooperative launch; each CTA owns a contiguous row range.  The basis
+// is stored as 4-column panels (panel p holds columns 4p..4p+3 as an n x 4
+// row-major array), so 32 consecutive rows of a panel are one contiguous
+// 16-byte-per-row run.  A warp takes 32-row blocks in two phases:
+//   phase A, one lane per row: load the row's panels (coalesced 512-byte
+//     warp loads), subtract V c (coefficients broadcast from shared memory),
+//     store the row, add its Gram entries;
+//   phase B, LPR lanes per row, lane p holding panel p: add the row's
+//     products to the new coefficients V^T u (the panels come back from L1/L2).
+// FP32 path: inner products in FP32 windows carried by TwoSum and combined
+// over lanes by a TwoSum tree, then in FP64 over warps and CTAs in a fixed
+// order (bitwise reproducible).  FP64 path: FP64 throughout.
 #include "common.cuh"
 #include "internal.h"
 
 namespace sfairsc {
 
-// 2-D tiled bulk copy of a box {Jc columns, rows} of V into shared memory.
-__device__ __forceinline__ void tensor_g2s_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
-          "r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
+namespace {
+
+constexpr int kOT = 512;  // threads per CTA
+constexpr int kOW = kOT / 32;
+constexpr int kCoefMax = 256 * 4;  // J * B
+constexpr int kNormOff = kCoefMax, kGramOff = kCoefMax + 4, kGram2Off = kCoefMax + 20, kStride = kCoefMax + 36;
+// per-warp partials: coefficients + 16 extras (J <= 128 columns when NC = 1)
+template <int NC>
+constexpr int red_stride() {
+  return (NC == 1 ? 128 * 4 : kCoefMax) + 16;
 }
 
+// Accumulator: a window in VT plus a carry (TwoSum pair for FP32, plain FP64 for FP64).
 template <typename VT>
-struct OrthArgs {
-  int n;
-  int64_t ldv;
-  VT* V;
-  VT* U;  // row-major n x 4
-  VT* Q;  // row-major n x 4, copy of the new block
-  double* H;
-  int ldh;
-  double* partial;
-  double* coef;
-  const int32_t* __restrict__ cta_rows;
-  GridBarrier bar;
-  unsigned* err;
-  int* brk_step;
-  int* sweeps;
-  int J, j;
+struct Acc;
+template <>
+struct Acc<float> {
+  float w;
+  Comp32 k;
+  __device__ __forceinline__ void zero() {
+    w = 0.f;
+    k.zero();
+  }
+  __device__ __forceinline__ void fma_(float x, float y) { w = fmaf(x, y, w); }
+  __device__ __forceinline__ void flush() {
+    k.add(w);
+    w = 0.f;
+  }
+  __device__ __forceinline__ void reduce(int from) {
+    flush();
+    k.reduce(from);
+  }
+  __device__ __forceinline__ double value() const { return k.value(); }
+};
+template <>
+struct Acc<double> {
+  double w;
+  __device__ __forceinline__ void zero() { w = 0.0; }
+  __device__ __forceinline__ void fma_(double x, double y) { w = fma(x, y, w); }
+  __device__ __forceinline__ void flush() {}
+  __device__ __forceinline__ void reduce(int from) {
+    for (int o = from; o < 32; o <<= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+  }
+  __device__ __forceinline__ double value() const { return w; }
 };
 
-template <typename VT, int NC>
-struct OrthShape {
-  static constexpr int kThreads = 512;
-  static constexpr int kWarps = kThreads / 32;
-  static constexpr int kRowsPerWarp = (sizeof(VT) == 4 ? 4 : 2) / NC;
-  static constexpr int kGroupRows = kWarps * kRowsPerWarp;  // rows per ring stage
-  static constexpr int kCols = 128 * NC;                     // columns one warp covers
-  static constexpr int kStages = NC == 1 ? 3 : 2;  // ring + per-warp sums stay under 227 KB
-  static constexpr size_t kStageElems = (size_t)kGroupRows * kCols + (size_t)kGroupRows * 4;  // V box + U rows
-};
-
 template <typename VT>
-__device__ __forceinline__ void lds_row4(const VT* p, VT (&x)[4]) {
+__device__ __forceinline__ void ld4(const VT* p, VT (&x)[4]) {
   if constexpr (sizeof(VT) == 4) {
     const float4 v = *reinterpret_cast<const float4*>(p);
-    x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+    x[0] = v.x;
+    x[1] = v.y;
+    x[2] = v.z;
+    x[3] = v.w;
   } else {
     const double2 a = reinterpret_cast<const double2*>(p)[0];
     const double2 b = reinterpret_cast<const double2*>(p)[1];
-    x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
+    x[0] = a.x;
+    x[1] = a.y;
+    x[2] = b.x;
+    x[3] = b.y;
+  }
+}
+template <typename VT>
+__device__ __forceinline__ void st4(VT* p, const VT (&x)[4]) {
+  if constexpr (sizeof(VT) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
+  } else {
+    reinterpret_cast<double2*>(p)[0] = make_double2(x[0], x[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(x[2], x[3]);
   }
 }
 
-template <typename VT, int B>
-__device__ __forceinline__ void load_u(const VT* U, int r, VT (&u)[B]) {
-  if constexpr (sizeof(VT) == 4 && B == 4) {
-    const float4 v = *reinterpret_cast<const float4*>(U + (size_t)r * 4);
-    u[0] = v.x; u[1] = v.y; u[2] = v.z; u[3] = v.w;
-  } else {
-#pragma unroll
-    for (int v = 0; v < B; ++v) u[v] = U[(size_t)r * 4 + v];
-  }
+__device__ __forceinline__ int lanes_for(int np) {
+  return np <= 1 ? 1 : np <= 2 ? 2 : np <= 4 ? 4 : np <= 8 ? 8 : np <= 16 ? 16 : 32;
 }
 
 // CTA b owns pairs p = b, b + grid, ...; sums partial[i][p] over CTAs i in
@@ -125,271 +141,236 @@ __device__ __forceinline__ void reduce_all(const double* partial, int stride, in
   __syncthreads();
 }
 
-constexpr int kWindow = 64;
+}  // namespace
+
+template <typename VT>
+struct OrthArgs {
+  int n;
+  VT* V;  // panels of n x 4
+  VT* U;  // row-major n x 4
+  VT* Q;  // row-major n x 4, copy of the new block
+  double* H;
+  int ldh;
+  double* partial;
+  double* coef;
+  const int32_t* __restrict__ cta_rows;
+  GridBarrier bar;
+  unsigned* err;
+  int* brk_step;
+  int* sweeps;
+  int J, j;
+};
+
+// Shared memory: coefficients (kCoefMax VT), per-warp partials (kOW x
+// red_stride doubles), reduction scratch (1024 doubles), per-warp updated rows
+// (kOW x 32 x 4 VT).  Kept small so that L1 holds the panels phase B re-reads.
+template <typename VT, int NC>
+constexpr size_t orth_smem_bytes() {
+  return sizeof(VT) * kCoefMax + sizeof(double) * ((size_t)kOW * red_stride<NC>() + 1024) + sizeof(VT) * kOW * 32 * 4 +
+         256;
+}
 
 template <typename VT, int B, int NC>
-__global__ void __launch_bounds__(512, 1) orth_kernel(OrthArgs<VT> a, const __grid_constant__ CUtensorMap vmap) {
-  using S = OrthShape<VT, NC>;
-  extern __shared__ __align__(128) unsigned char smraw[];
-  unsigned char* sm = smraw + ((128u - (smem_u32(smraw) & 127u)) & 127u);  // 128-byte aligned stages
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int CW = S::kCols;
-  VT* ring = reinterpret_cast<VT*>(sm);                                                   // stages
-  double* tot = reinterpret_cast<double*>(sm + sizeof(VT) * S::kStages * S::kStageElems);  // warps x CW x B
-  double* scratch = tot + (size_t)S::kWarps * CW * B;                                     // 512
-  __shared__ __align__(8) uint64_t full[S::kStages], empty[S::kStages];
+__global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  VT* cfs = reinterpret_cast<VT*>(smraw);                                  // coefficients c*B + v
+  constexpr int kRed = red_stride<NC>();
+  constexpr int kXo = kRed - 16;                                           // extras offset
+  double* red = reinterpret_cast<double*>(smraw + sizeof(VT) * kCoefMax);  // kOW x kRed
+  double* scratch = red + (size_t)kOW * kRed;                              // 1024
+  VT* uws = reinterpret_cast<VT*>(scratch + 1024);                         // kOW x 32 x 4
   __shared__ double gram_s[16], R1[16], R2[16], Rd1[16], Rd2[16], unorm[4];
-  __shared__ int brk, again, abort_flag;
-
+  __shared__ int brk, again;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int r0 = a.cta_rows[blockIdx.x], r1 = a.cta_rows[blockIdx.x + 1];
   const int J = a.J, P = J * B;
-  const int Jc = (J + 3) & ~3;
-  const int kNorm = CW * B, kGram = kNorm + 4, kGram2 = kGram + 16, stride = kGram2 + 16;
+  const int np = (J + 3) / 4;  // panels holding columns 0..J-1
+  const size_t pn = (size_t)a.n * 4;
+  constexpr int NG = B * (B + 1) / 2;  // unique Gram entries
+  constexpr int NA = NG > B ? NG : B;
   VT* U = a.U;
-  if (threadIdx.x == 0) {
-    brk = 0;
-    for (int s = 0; s < S::kStages; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], S::kWarps);
-    }
-    mbar_fence_init();
-  }
+  VT* uw = uws + (size_t)warp * 32 * 4;
+  if (threadIdx.x == 0) brk = 0;
   __syncthreads();
-  long seq = 0;  // ring groups issued so far (same value in every thread)
 
-  auto colof = [&](int q, int i) { return 128 * q + 4 * lane + i; };
-
-  // Stream the CTA's rows of V[:, 0:Jc] through the ring; consume(r, row_in_smem) per row.
-  auto stream = [&](auto&& consume) -> bool {
-    const int ngroups = (r1 - r0 + S::kGroupRows - 1) / S::kGroupRows;
-    const unsigned rowbytes = (unsigned)(Jc * sizeof(VT));
-    auto issue = [&](int g) {
-      // one tiled copy of rows rg..rg+kGroupRows-1, columns 0..Jc-1 (rows past n read as zero),
-      // and one linear copy of the same rows of U (clipped at n)
-      const int s = (int)((seq + g) % S::kStages);
-      const int rg = r0 + g * S::kGroupRows;
-      const int nu = min(S::kGroupRows, a.n - rg);
-      const unsigned ubytes = (unsigned)(nu * 4 * sizeof(VT));
-      VT* st = ring + (size_t)s * S::kStageElems;
-      mbar_arrive_expect_tx(&full[s], (unsigned)S::kGroupRows * rowbytes + ubytes);
-      tensor_g2s_2d(st, &vmap, 0, rg, &full[s]);
-      bulk_g2s(st + (size_t)S::kGroupRows * S::kCols, U + (size_t)rg * 4, ubytes, &full[s]);
-    };
-    if (threadIdx.x == 0) {
-      fence_proxy_async();
-      for (int g = 0; g < min(S::kStages, ngroups); ++g) issue(g);
-    }
-    if (threadIdx.x == 0) abort_flag = 0;
-    __syncthreads();
-    int g = 0;
-    for (; g < ngroups; ++g) {
-      const long q = seq + g;
-      const int s = (int)(q % S::kStages);
-      const unsigned par = (unsigned)((q / S::kStages) & 1);
-      if (!mbar_wait(&full[s], par, a.err)) atomicExch(&abort_flag, 1);
-      if (*(volatile int*)&abort_flag) break;
-      const VT* stage = ring + (size_t)s * S::kStageElems;
-      const int rw = r0 + g * S::kGroupRows + warp * S::kRowsPerWarp;
-      consume(rw, stage + (size_t)warp * S::kRowsPerWarp * Jc,
-              stage + (size_t)S::kGroupRows * S::kCols + (size_t)warp * S::kRowsPerWarp * 4);
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[s]);
-      if (threadIdx.x == 0 && g + S::kStages < ngroups) {
-        if (mbar_wait(&empty[s], par, a.err)) {
-          fence_proxy_async();
-          issue(g + S::kStages);
-        } else {
-          atomicExch(&abort_flag, 1);
-        }
-      }
-    }
-    __syncthreads();
-    if (abort_flag) {
-      // drain: wait (bounded) for every copy this CTA issued before returning
-      if (threadIdx.x == 0) {
-        for (int gg = 0; gg < ngroups; ++gg) {
-          const long q = seq + gg;
-          if (!mbar_try_wait(&full[(int)(q % S::kStages)], (unsigned)((q / S::kStages) & 1)))
-            mbar_wait(&full[(int)(q % S::kStages)], (unsigned)((q / S::kStages) & 1), a.err, 100000000ull);
-        }
-      }
+  // sweep kinds: 0 = coefficients + input norms; 1 = update with a.coef, then the
+  // next coefficients and the Gram matrix; 2 = update with a.coef, then the Gram matrix.
+  auto sweep = [&](int kind) {
+    const bool upd = kind >= 1, want_c = kind <= 1;
+    if (upd) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) cfs[i] = (VT)__ldcg(a.coef + i);
       __syncthreads();
-      return false;
     }
-    seq += ngroups;
-    __syncthreads();
-    return true;
-  };
-
-  auto zero_tot = [&]() {
-    for (int i = lane; i < CW * B; i += 32) tot[(size_t)warp * CW * B + i] = 0.0;
-    __syncwarp();
-  };
-  // CTA partial of the column sums (columns < J), warps in order.
-  auto store_tot = [&]() {
-    __syncthreads();
-    for (int p = threadIdx.x; p < P; p += blockDim.x) {
-      double s = 0.0;
-      for (int w = 0; w < S::kWarps; ++w) s += tot[(size_t)w * CW * B + p];
-      a.partial[(size_t)blockIdx.x * stride + p] = s;
-    }
-  };
-  auto store_small = [&](double val, int cnt, int off) {
-    // lanes t < cnt of every warp hold val; CTA sum to partial[off + t]
-    __syncthreads();
-    if (lane < cnt) scratch[warp * 16 + lane] = val;
-    __syncthreads();
-    if ((int)threadIdx.x < cnt) {
-      double s = 0.0;
-      for (int w = 0; w < S::kWarps; ++w) s += scratch[w * 16 + threadIdx.x];
-      a.partial[(size_t)blockIdx.x * stride + off + threadIdx.x] = s;
-    }
-  };
-
-  // sweep kinds: 0 = coefficients (+ input norms); 1 = update with a.coef, then
-  // next coefficients and Gram; 2 = update with a.coef, then Gram only.
-  auto sweep = [&](int kind) -> bool {
-    VT cr[NC][4][B];
+    const int LPR = NC == 1 ? lanes_for(np) : 32;
+    const int RPW = 32 / LPR;
+    const int p0 = lane & (LPR - 1), ri = lane / LPR;
+    Acc<VT> acc[NC][4][B];
+    Acc<VT> ga[NA];
 #pragma unroll
     for (int q = 0; q < NC; ++q)
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int jj = 0; jj < 4; ++jj)
 #pragma unroll
-        for (int v = 0; v < B; ++v) {
-          const int c = colof(q, i);
-          cr[q][i][v] = (kind > 0 && c < J) ? (VT)__ldcg(a.coef + (size_t)c * B + v) : VT(0);
-        }
-    if (kind < 2) zero_tot();
-    VT win[NC][4][B];
+        for (int v = 0; v < B; ++v) acc[q][jj][v].zero();
 #pragma unroll
-    for (int q = 0; q < NC; ++q)
+    for (int e = 0; e < NA; ++e) ga[e].zero();
+    int nb = 0;
+    for (int rb = r0 + warp * 32; rb < r1; rb += kOW * 32) {
+      // ---- phase A: lane = row
+      const int r = rb + lane;
+      VT u[4] = {VT(0), VT(0), VT(0), VT(0)};
+      if (r < r1) {
+        ld4(U + (size_t)r * 4, u);
+        if (upd) {
+          VT d[B];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+          for (int v = 0; v < B; ++v) d[v] = VT(0);
+          const int nfull = J >> 2;  // panels whose 4 columns are all < J
+#pragma unroll 8
+          for (int pp = 0; pp < nfull; ++pp) {
+            VT x[4];
+            ld4(a.V + pp * pn + (size_t)r * 4, x);
 #pragma unroll
-        for (int v = 0; v < B; ++v) win[q][i][v] = VT(0);
-    double side = 0.0;  // lanes < B: input norms (kind 0); lanes < B*B: Gram (kinds 1, 2)
-    VT sidew = VT(0);   // its FP32 window
-    int cnt = 0;
-    auto flush = [&]() {
-      side += (double)sidew;
-      sidew = VT(0);
-      if (kind == 2) return;
+            for (int jj = 0; jj < 4; ++jj)
 #pragma unroll
-      for (int q = 0; q < NC; ++q)
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int v = 0; v < B; ++v) {
-            tot[((size_t)warp * CW + colof(q, i)) * B + v] += (double)win[q][i][v];
-            win[q][i][v] = VT(0);
+              for (int v = 0; v < B; ++v) d[v] = fma(x[jj], cfs[(4 * pp + jj) * B + v], d[v]);
           }
-    };
-    const bool ok = stream([&](int rw, const VT* rows, const VT* us) {
-      constexpr int R = S::kRowsPerWarp;
-      VT x[R][NC][4];
-      VT u[R][B];
-      bool live[R];
+          if (nfull < np) {
+            VT x[4];
+            ld4(a.V + nfull * pn + (size_t)r * 4, x);
+            for (int jj = 0; jj < (J & 3); ++jj)
 #pragma unroll
-      for (int t = 0; t < R; ++t) {
-        live[t] = rw + t < r1;
-#pragma unroll
-        for (int q = 0; q < NC; ++q) {
-          if (colof(q, 0) < Jc) {
-            lds_row4(rows + (size_t)t * Jc + colof(q, 0), x[t][q]);
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-              if (colof(q, i) >= J || !live[t]) x[t][q][i] = VT(0);
-          } else {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) x[t][q][i] = VT(0);
+              for (int v = 0; v < B; ++v) d[v] = fma(x[jj], cfs[(4 * nfull + jj) * B + v], d[v]);
           }
-        }
 #pragma unroll
-        for (int v = 0; v < B; ++v) u[t][v] = live[t] ? us[t * 4 + v] : VT(0);
+          for (int v = 0; v < B; ++v) u[v] -= d[v];
+          st4(U + (size_t)r * 4, u);
+        } else {
+          for (int pp = 0; pp < np; ++pp) asm volatile("prefetch.global.L1 [%0];" ::"l"(a.V + pp * pn + (size_t)r * 4));
+        }
       }
-      if (kind > 0) {
-        VT d[R][B];
+      if (kind == 0) {
 #pragma unroll
-        for (int t = 0; t < R; ++t)
-#pragma unroll
-          for (int v = 0; v < B; ++v) d[t][v] = VT(0);
-#pragma unroll
-        for (int t = 0; t < R; ++t)
-#pragma unroll
-          for (int q = 0; q < NC; ++q)
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-              for (int v = 0; v < B; ++v) d[t][v] = fma(x[t][q][i], cr[q][i][v], d[t][v]);
-        // interleaved butterfly reductions of all R x B partial dots
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-          for (int t = 0; t < R; ++t)
-#pragma unroll
-            for (int v = 0; v < B; ++v) d[t][v] += __shfl_xor_sync(0xffffffffu, d[t][v], o);
-#pragma unroll
-        for (int t = 0; t < R; ++t) {
-#pragma unroll
-          for (int v = 0; v < B; ++v) u[t][v] -= d[t][v];
-          if (lane == 0 && live[t]) {
-#pragma unroll
-            for (int v = 0; v < B; ++v) U[(size_t)(rw + t) * 4 + v] = u[t][v];
-          }
-          VT ua = VT(0), ub = VT(0);
-#pragma unroll
-          for (int v = 0; v < B; ++v)
-#pragma unroll
-            for (int w2 = 0; w2 < B; ++w2)
-              if (lane == v * B + w2) {
-                ua = u[t][v];
-                ub = u[t][w2];
-              }
-          sidew = fma(ua, ub, sidew);
-        }
+        for (int v = 0; v < B; ++v) ga[v].fma_(u[v], u[v]);
       } else {
+        int e = 0;
 #pragma unroll
-        for (int t = 0; t < R; ++t) {
-          VT uu = VT(0);
+        for (int v = 0; v < B; ++v)
 #pragma unroll
-          for (int v = 0; v < B; ++v) uu = lane == v ? u[t][v] : uu;
-          sidew = fma(uu, uu, sidew);
+          for (int w2 = v; w2 < B; ++w2) ga[e++].fma_(u[v], u[w2]);
+      }
+      if (want_c) st4(uw + lane * 4, u);
+      __syncwarp();
+      // ---- phase B: LPR lanes per row, lane p0 (+32 q) holding panel p0 (+32 q)
+      if (want_c) {
+        const int nrow = min(32, r1 - rb);
+        for (int s0 = 0; s0 < LPR; s0 += 4) {
+          // four rows' loads in flight before their products
+          VT xs[4][NC][4], us[4][4];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const int i = ri + RPW * (s0 + t);
+            const bool in = s0 + t < LPR && i < nrow;
+            if (in) ld4(uw + i * 4, us[t]);
+            else us[t][0] = us[t][1] = us[t][2] = us[t][3] = VT(0);
+#pragma unroll
+            for (int q = 0; q < NC; ++q) {
+              const int pp = p0 + 32 * q;
+              if (in && pp < np) {
+                ld4(a.V + pp * pn + (size_t)(rb + i) * 4, xs[t][q]);
+                if (4 * pp + 4 > J)
+#pragma unroll
+                  for (int jj = 0; jj < 4; ++jj)
+                    if (4 * pp + jj >= J) xs[t][q][jj] = VT(0);
+              } else {
+                xs[t][q][0] = xs[t][q][1] = xs[t][q][2] = xs[t][q][3] = VT(0);
+              }
+            }
+          }
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+#pragma unroll
+            for (int q = 0; q < NC; ++q)
+#pragma unroll
+              for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+                for (int v = 0; v < B; ++v) acc[q][jj][v].fma_(xs[t][q][jj], us[t][v]);
         }
       }
-      if (kind < 2) {
+      __syncwarp();
+      if (++nb == 4) {
 #pragma unroll
-        for (int t = 0; t < R; ++t)
+        for (int q = 0; q < NC; ++q)
 #pragma unroll
-          for (int q = 0; q < NC; ++q)
+          for (int jj = 0; jj < 4; ++jj)
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int v = 0; v < B; ++v) acc[q][jj][v].flush();
 #pragma unroll
-              for (int v = 0; v < B; ++v) win[q][i][v] = fma(x[t][q][i], u[t][v], win[q][i][v]);
+        for (int e = 0; e < NA; ++e) ga[e].flush();
+        nb = 0;
       }
-      cnt += R;
-      if (cnt >= kWindow) {
-        flush();
-        cnt = 0;
+    }
+    // ---- combine over the warp's lanes, then over warps into this CTA's partial
+#pragma unroll
+    for (int q = 0; q < NC; ++q)
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+        for (int v = 0; v < B; ++v) acc[q][jj][v].reduce(LPR);
+#pragma unroll
+    for (int e = 0; e < NA; ++e) ga[e].reduce(1);
+    double* rw = red + (size_t)warp * kRed;
+    if (want_c && ri == 0)
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        const int pp = p0 + 32 * q;
+        if (pp < np)
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj)
+            if (4 * pp + jj < J)
+#pragma unroll
+              for (int v = 0; v < B; ++v) rw[(4 * pp + jj) * B + v] = acc[q][jj][v].value();
       }
-    });
-    if (!ok) return false;
-    flush();
-    if (kind < 2) store_tot();
-    if (kind == 0) store_small(side, B, kNorm);
-    else store_small(side, B * B, kGram);
-    return true;
+    if (lane == 0) {
+      if (kind == 0) {
+#pragma unroll
+        for (int v = 0; v < B; ++v) rw[kXo + v] = ga[v].value();
+      } else {
+        int e = 0;
+#pragma unroll
+        for (int v = 0; v < B; ++v)
+#pragma unroll
+          for (int w2 = v; w2 < B; ++w2) {
+            const double g = ga[e++].value();
+            rw[kXo + v * B + w2] = g;
+            rw[kXo + w2 * B + v] = g;
+          }
+      }
+    }
+    __syncthreads();
+    if (want_c)
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        double s = 0.0;
+        for (int w = 0; w < kOW; ++w) s += red[(size_t)w * kRed + i];
+        a.partial[(size_t)blockIdx.x * kStride + i] = s;
+      }
+    const int ne = kind == 0 ? B : B * B;
+    if ((int)threadIdx.x < ne) {
+      double s = 0.0;
+      for (int w = 0; w < kOW; ++w) s += red[(size_t)w * kRed + kXo + threadIdx.x];
+      a.partial[(size_t)blockIdx.x * kStride + (kind == 0 ? kNormOff : kGramOff) + threadIdx.x] = s;
+    }
   };
 
   // Thread-per-row Gram of U (B x B) to partial[off..], optionally after U <- U R1^{-1}.
   auto gram_rows = [&](int off, bool apply_r1) {
-    double gacc[B][B];
+    Acc<VT> g[NG];
 #pragma unroll
-    for (int v = 0; v < B; ++v)
-#pragma unroll
-      for (int w2 = 0; w2 < B; ++w2) gacc[v][w2] = 0.0;
+    for (int e = 0; e < NG; ++e) g[e].zero();
+    int nb = 0;
     for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-      VT u[B];
-      load_u<VT, B>(U, r, u);
+      VT u[4];
+      ld4(U + (size_t)r * 4, u);
       if (apply_r1) {
 #pragma unroll
         for (int v = 0; v < B; ++v) {
@@ -398,27 +379,38 @@ __global__ void __launch_bounds__(512, 1) orth_kernel(OrthArgs<VT> a, const __gr
           for (int q = 0; q < v; ++q) s -= u[q] * (VT)Rd1[q * B + v];
           u[v] = s / (VT)Rd1[v * B + v];
         }
-#pragma unroll
-        for (int v = 0; v < B; ++v) U[(size_t)r * 4 + v] = u[v];
+        st4(U + (size_t)r * 4, u);
       }
+      int e = 0;
 #pragma unroll
       for (int v = 0; v < B; ++v)
 #pragma unroll
-        for (int w2 = 0; w2 < B; ++w2) gacc[v][w2] = fma((double)u[v], (double)u[w2], gacc[v][w2]);
+        for (int w2 = v; w2 < B; ++w2) g[e++].fma_(u[v], u[w2]);
+      if (++nb == 16) {
+#pragma unroll
+        for (int ee = 0; ee < NG; ++ee) g[ee].flush();
+        nb = 0;
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < NG; ++e) g[e].reduce(1);
+    __syncthreads();
+    if (lane == 0) {
+      int e = 0;
+#pragma unroll
+      for (int v = 0; v < B; ++v)
+#pragma unroll
+        for (int w2 = v; w2 < B; ++w2) {
+          const double x = g[e++].value();
+          scratch[warp * 16 + v * B + w2] = x;
+          scratch[warp * 16 + w2 * B + v] = x;
+        }
     }
     __syncthreads();
-#pragma unroll
-    for (int v = 0; v < B; ++v)
-#pragma unroll
-      for (int w2 = 0; w2 < B; ++w2) {
-        const double s = warp_allsum(gacc[v][w2]);
-        if (lane == 0) scratch[warp * 16 + v * B + w2] = s;
-      }
-    __syncthreads();
-    if (threadIdx.x < B * B) {
+    if ((int)threadIdx.x < B * B) {
       double s = 0.0;
-      for (int w = 0; w < S::kWarps; ++w) s += scratch[w * 16 + threadIdx.x];
-      a.partial[(size_t)blockIdx.x * stride + off + threadIdx.x] = s;
+      for (int w = 0; w < kOW; ++w) s += scratch[w * 16 + threadIdx.x];
+      a.partial[(size_t)blockIdx.x * kStride + off + threadIdx.x] = s;
     }
   };
 
@@ -456,19 +448,19 @@ __global__ void __launch_bounds__(512, 1) orth_kernel(OrthArgs<VT> a, const __gr
   int sweeps = 0;
   if (J > 0) {
     // sweep 1: c1 = V^T U and the input norms
-    if (!sweep(0)) return;
+    sweep(0);
     ++sweeps;
     if (!grid_sync(a.bar, a.err)) return;
-    reduce_owned(a.partial, stride, P, a.coef, scratch);
+    reduce_owned(a.partial, kStride, P, a.coef, scratch);
     if (a.j >= 0)
       for (int p = blockIdx.x; p < P; p += gridDim.x) a.H[(size_t)(p / B) + (size_t)a.ldh * (a.j + p % B)] = a.coef[p];
-    reduce_all(a.partial, stride, kNorm, B, unorm);
+    reduce_all(a.partial, kStride, kNormOff, B, unorm);
     if (!grid_sync(a.bar, a.err)) return;
     // sweep 2: U -= V c1; c2 = V^T U; Gram
-    if (!sweep(1)) return;
+    sweep(1);
     ++sweeps;
     if (!grid_sync(a.bar, a.err)) return;
-    reduce_all(a.partial, stride, kGram, B * B, gram_s);
+    reduce_all(a.partial, kStride, kGramOff, B * B, gram_s);
     if (threadIdx.x == 0) {
       again = 0;
       for (int v = 0; v < B; ++v)
@@ -476,29 +468,29 @@ __global__ void __launch_bounds__(512, 1) orth_kernel(OrthArgs<VT> a, const __gr
     }
     __syncthreads();
     if (again) {
-      reduce_owned(a.partial, stride, P, a.coef, scratch);
+      reduce_owned(a.partial, kStride, P, a.coef, scratch);
       if (a.j >= 0)
         for (int p = blockIdx.x; p < P; p += gridDim.x) a.H[(size_t)(p / B) + (size_t)a.ldh * (a.j + p % B)] += a.coef[p];
       if (!grid_sync(a.bar, a.err)) return;
       // sweep 3: U -= V c2; Gram
-      if (!sweep(2)) return;
+      sweep(2);
       ++sweeps;
       if (!grid_sync(a.bar, a.err)) return;
-      reduce_all(a.partial, stride, kGram, B * B, gram_s);
+      reduce_all(a.partial, kStride, kGramOff, B * B, gram_s);
     }
   } else {
     if (threadIdx.x < B) unorm[threadIdx.x] = 0.0;
-    gram_rows(kGram, false);
+    gram_rows(kGramOff, false);
     if (!grid_sync(a.bar, a.err)) return;
-    reduce_all(a.partial, stride, kGram, B * B, gram_s);
+    reduce_all(a.partial, kStride, kGramOff, B * B, gram_s);
   }
   cholesky(R1, Rd1);
 
   if (B > 1) {
     // Cholesky QR a second time: U <- U R1^{-1}, Gram again
-    gram_rows(kGram2, true);
+    gram_rows(kGram2Off, true);
     if (!grid_sync(a.bar, a.err)) return;
-    reduce_all(a.partial, stride, kGram2, B * B, gram_s);
+    reduce_all(a.partial, kStride, kGram2Off, B * B, gram_s);
     if (threadIdx.x < B) unorm[threadIdx.x] = 0.0;
     __syncthreads();
     cholesky(R2, Rd2);
@@ -510,10 +502,12 @@ __global__ void __launch_bounds__(512, 1) orth_kernel(OrthArgs<VT> a, const __gr
     __syncthreads();
   }
 
-  // V[:, J:J+B] = U R^{-1} and its copy Q
+  // V[:, J:J+B] = U R^{-1} (inside panel J/4: J % 4 + B <= 4) and its copy Q
+  VT* Vp = a.V + (size_t)(J / 4) * pn;
+  const int c0 = J & 3;
   for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-    VT u[B];
-    load_u<VT, B>(U, r, u);
+    VT u[4];
+    ld4(U + (size_t)r * 4, u);
     if (B > 1) {
 #pragma unroll
       for (int v = 0; v < B; ++v) {
@@ -527,7 +521,7 @@ __global__ void __launch_bounds__(512, 1) orth_kernel(OrthArgs<VT> a, const __gr
     }
 #pragma unroll
     for (int v = 0; v < B; ++v) {
-      a.V[(size_t)r * a.ldv + J + v] = u[v];
+      Vp[(size_t)r * 4 + c0 + v] = u[v];
       a.Q[(size_t)r * 4 + v] = u[v];
     }
   }
@@ -553,38 +547,9 @@ __global__ void __launch_bounds__(512, 1) orth_kernel(OrthArgs<VT> a, const __gr
 }
 
 template <typename VT, int B, int NC>
-static size_t orth_smem() {
-  using S = OrthShape<VT, NC>;
-  return sizeof(VT) * S::kStages * S::kStageElems + sizeof(double) * ((size_t)S::kWarps * S::kCols * B + 512) + 256;
-}
-
-// Tensor map of the basis V (row-major n x ldv) with a box of Jc columns x rows.
-static void make_vmap(CUtensorMap* map, bool f64, void* V, int n, int64_t ldv, int Jc, int rows) {
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  if (!encode) {
-    void* fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    check_cuda(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q),
-               "driver entry point cuTensorMapEncodeTiled");
-    if (!fn || q != cudaDriverEntryPointSuccess) fail(SFAIRSC_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
-    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  }
-  const size_t vs = f64 ? 8 : 4;
-  const cuuint64_t dims[2] = {(cuuint64_t)ldv, (cuuint64_t)n};
-  const cuuint64_t strides[1] = {(cuuint64_t)(ldv * vs)};
-  const cuuint32_t box[2] = {(cuuint32_t)Jc, (cuuint32_t)rows};
-  const cuuint32_t estr[2] = {1, 1};
-  const CUresult r = encode(map, f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, V, dims,
-                            strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) fail(SFAIRSC_ERR_CUDA, "cuTensorMapEncodeTiled failed for the basis");
-}
-
-template <typename VT, int B, int NC>
 static void orth_launch_t(const OrthPlan& p, int J, int j, cudaStream_t s) {
   OrthArgs<VT> a;
   a.n = p.n;
-  a.ldv = p.ldv;
   a.V = static_cast<VT*>(p.V);
   a.U = static_cast<VT*>(p.U);
   a.Q = static_cast<VT*>(p.Q);
@@ -599,15 +564,11 @@ static void orth_launch_t(const OrthPlan& p, int J, int j, cudaStream_t s) {
   a.sweeps = p.sweeps;
   a.J = J;
   a.j = j;
-  const size_t smem = orth_smem<VT, B, NC>();
+  const size_t smem = orth_smem_bytes<VT, NC>();
   auto kern = orth_kernel<VT, B, NC>;
   check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "orth smem attr");
-  alignas(64) CUtensorMap vmap;
-  const int Jc = (J + 3) & ~3;
-  make_vmap(&vmap, sizeof(VT) == 8, p.V, p.n, p.ldv, Jc > 0 ? Jc : 4, OrthShape<VT, NC>::kGroupRows);
-  void* args[] = {&a, &vmap};
-  check_cuda(cudaLaunchCooperativeKernel((void*)kern, dim3(p.grid), dim3(OrthShape<VT, NC>::kThreads), args, smem, s),
-             "orth cooperative launch");
+  void* args[] = {&a};
+  check_cuda(cudaLaunchCooperativeKernel((void*)kern, dim3(p.grid), dim3(kOT), args, smem, s), "orth cooperative launch");
 }
 
 template <typename VT, int B>
@@ -618,7 +579,7 @@ static void orth_launch_b(const OrthPlan& p, int J, int j, cudaStream_t s) {
 
 void launch_orth(const OrthPlan& p, VecType vt, int J, int j, int B, cudaStream_t s) {
   if (J > 256) fail(SFAIRSC_ERR_UNSUPPORTED, "Krylov basis larger than 256 columns");
-  if (p.ldv % 4 != 0) fail(SFAIRSC_ERR_UNSUPPORTED, "basis leading dimension must be a multiple of 4");
+  if ((J & 3) + B > 4) fail(SFAIRSC_ERR_UNSUPPORTED, "a new block must fit in one 4-column panel");
   if (vt == VecType::F64) {
     if (B == 1) orth_launch_b<double, 1>(p, J, j, s);
     else if (B == 2) orth_launch_b<double, 2>(p, J, j, s);
@@ -633,11 +594,10 @@ void launch_orth(const OrthPlan& p, VecType vt, int J, int j, int B, cudaStream_
 template <typename VT, int B, int NC>
 static int orth_grid_t() {
   auto kern = orth_kernel<VT, B, NC>;
-  const size_t smem = orth_smem<VT, B, NC>();
+  const size_t smem = orth_smem_bytes<VT, NC>();
   check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "orth smem attr");
   int per_sm = 0, dev = 0, sms = 0;
-  check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, OrthShape<VT, NC>::kThreads, smem),
-             "orth occupancy");
+  check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kOT, smem), "orth occupancy");
   check_cuda(cudaGetDevice(&dev), "get device");
   check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "sm count");
   return per_sm * sms;

@@ -34,7 +34,7 @@ struct StaticScratch {
   double params[kParams];
   int32_t cta_rows[kStaticMaxGrid + 1];
   uint8_t lab[kStaticMaxN];
-  unsigned words[8];  // [0] validation flags, [1] degree flags, [2..3] barrier, [4] kernel error word
+  unsigned words[8];  // [0] validation flags, [1] degree flags, [2..3] barrier, [4] kernel error word, [5] SpMV work
 };
 
 static __device__ __align__(256) StaticScratch g_static_scratch;
@@ -150,6 +150,7 @@ static int apply_static(int64_t n64, int64_t nnz, const int32_t* row_ptr, const 
   double sigma = 0.0;
   for (int b = 0; b < (n + 255) / 256; ++b) sigma = std::max(sigma, g_host_blockmax[b]);
   P[kPSigma] = sigma;
+  for (int a = 0; a + 1 < h; ++a) P[kPLinv + a] = 1.0 / P[kPL + a * kLStride + a];
   check_cuda(cudaMemcpyAsync(S->params, P, sizeof(double) * kParams, cudaMemcpyHostToDevice, s), "h2d");
 
   // the fused operator, on the static scratch
@@ -167,7 +168,12 @@ static int apply_static(int64_t n64, int64_t nnz, const int32_t* row_ptr, const 
   o.grid = grid;
   o.threads = threads;
   o.batch_rows = (int)std::max(1ll, std::min(32ll, (long long)n / grid / 64));
-  o.lanes_per_row = 8;
+  {
+    const double avg = (double)nnz / (double)n;
+    int lanes = 2;
+    while (lanes < 32 && lanes * 8 < avg) lanes *= 2;
+    o.lanes_per_row = lanes;  // lanes per row of the SpMV, 8 entries per lane per pass
+  }
   o.row_ptr = row_ptr;
   o.col = col_idx;
   o.val = values;
@@ -181,6 +187,7 @@ static int apply_static(int64_t n64, int64_t nnz, const int32_t* row_ptr, const 
   o.cta_rows = S->cta_rows;
   o.barrier = barrier;
   o.err = err;
+  o.work = &S->words[5];
   launch_operator(o, VecType::F32, w, 1, n, out, 1, n, nvec, s);
   unsigned e = 0;
   check_cuda(cudaMemcpyAsync(&e, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "d2h");
