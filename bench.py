@@ -446,7 +446,9 @@ def run_ours(args):
         "solve": {"restarts": inf["restarts"], "matvecs": inf["matvecs"], "max_resid": inf["max_resid"],
                   "fairness_err": inf["fairness_err"], "dorth_err": inf["dorth_err"],
                   "ms_solve": inf["ms_solve"], "ms_kmeans": inf["ms_kmeans"], "kmeans_iters": inf["kmeans_iters"],
-                  "ms_operator_total": inf["ms_operator"], "ms_orth_total": inf["ms_orth"]},
+                  "ms_operator_total": inf["ms_operator"], "ms_orth_total": inf["ms_orth"],
+                  "ms_restart_total": inf["ms_restart"], "ms_host_eig_total": inf["ms_host_eig"],
+                  "ms_final": inf["ms_final"], "orth_sweeps": inf["orth_sweeps"], "n_orth": inf["n_orth"]},
         "operator_in_solve": {"achieved_gbs": op_gbs, "frac": op_gbs / peak, "ms_per_launch": op_avg_ms,
                               "bytes_per_launch": op_bytes},
     }
