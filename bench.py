@@ -133,6 +133,28 @@ def orth_bytes(n, sum_cols, launches, sweeps, s_x, b):
     return (sweeps / max(1, launches)) * n * s_x * sum_cols + launches * 2 * n * b * s_x
 
 
+def recorded_traffic(summary: str, sources: list[str]):
+    """DRAM bytes per launch from a committed ncu summary (profiles/), or None if
+    any of the kernel's source files changed since the counters were taken."""
+    import hashlib
+    import re
+
+    path = os.path.join(ROOT, "profiles", summary)
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*(\d+)", text)
+    if not m:
+        return None
+    for src in sources:
+        h = re.search(r"source_sha256 " + re.escape(os.path.basename(src)) + r":\s*([0-9a-f]{64})", text)
+        with open(os.path.join(ROOT, src), "rb") as f:
+            cur = hashlib.sha256(f.read()).hexdigest()
+        if not h or h.group(1) != cur:
+            return None
+    return int(m.group(1))
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -425,8 +447,12 @@ def run_ours(args):
     t_op = sum(i["ms_operator"] for i in infos)
     t_orth = sum(i["ms_orth"] for i in infos)
     if t_orth >= t_op:
+        traffic = None
+        if args.workload == "msbm_n1m_k50_h10" and args.scale == 1.0 and args.prec == "mixed" and args.block == 4:
+            traffic = recorded_traffic("orth_kernel_traffic_msbm_n1m_k50_h10.md",
+                                       ["paper_2210_16435_gb300/csrc/orth.cu", "paper_2210_16435_gb300/csrc/common.cuh"])
         roof = {"kernel": "orth_kernel (CGS2 + CholQR)", "bound": "hbm", "achieved": orth_gbs, "peak": peak,
-                "unit": "GB/s", "frac": orth_gbs / peak, "traffic": None,
+                "unit": "GB/s", "frac": orth_gbs / peak, "traffic": traffic,
                 "bytes_per_launch": orth_b, "ms_per_launch": orth_avg_ms}
     else:
         roof = {"kernel": "fused_operator_kernel", "bound": "hbm", "achieved": op_gbs, "peak": peak, "unit": "GB/s",
