@@ -108,6 +108,7 @@ struct sfairsc_ctx {
   OrthPlan orth;
   double* Hh = nullptr;  // pinned host copy of the projected matrix
   double* Yh = nullptr;  // pinned host
+  float* Yfh = nullptr;  // pinned host: FP32 copy of Y for the FP32 basis
 
   // results for backward / outputs
   double* X64 = nullptr;  // n x k column-major
@@ -155,6 +156,7 @@ struct sfairsc_ctx {
     for (void* p : owned) cudaFree(p);
     if (Hh) cudaFreeHost(Hh);
     if (Yh) cudaFreeHost(Yh);
+    if (Yfh) cudaFreeHost(Yfh);
     if (params_host) cudaFreeHost(params_host);
   }
 };
@@ -422,6 +424,7 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   q.sweeps = c->sweeps;
   check_cuda(cudaMallocHost((void**)&c->Hh, sizeof(double) * c->ldh * m), "pinned allocation");
   check_cuda(cudaMallocHost((void**)&c->Yh, sizeof(double) * m * m), "pinned allocation");
+  check_cuda(cudaMallocHost((void**)&c->Yfh, sizeof(float) * m * m), "pinned allocation");
 
   // final-stage buffers
   const int k = c->k;
@@ -518,6 +521,18 @@ struct Timer {
   }
 };
 
+// Y[:, 0:cols] (host, c->Yh) to the device in the basis precision (c->Yd holds
+// doubles, or floats in its first half for the FP32 basis).
+void upload_y(sfairsc_ctx* c, int mv, int cols) {
+  const size_t cnt = (size_t)mv * cols;
+  if (c->vt == VecType::F64) {
+    check_cuda(cudaMemcpyAsync(c->Yd, c->Yh, sizeof(double) * cnt, cudaMemcpyHostToDevice, c->stream), "h2d");
+  } else {
+    for (size_t i = 0; i < cnt; ++i) c->Yfh[i] = (float)c->Yh[i];
+    check_cuda(cudaMemcpyAsync(c->Yd, c->Yfh, sizeof(float) * cnt, cudaMemcpyHostToDevice, c->stream), "h2d");
+  }
+}
+
 // FP64 Ritz vectors X = V[:, 0:mv] Y[:, 0:k] -> project X <- P X (exact F^T H = 0)
 // -> AX = L_n^sigma X with the FP64 operator -> Rayleigh quotients and explicit
 // residual norms ||A x - lambda x|| / ||x||.  V is left untouched.
@@ -526,7 +541,7 @@ double final_check(sfairsc_ctx* c, int mv, const std::vector<double>& T, std::ve
   const int n = (int)c->n, k = c->k;
   for (int i = 0; i < k; ++i)
     for (int q = 0; q < mv; ++q) c->Yh[(size_t)i * mv + q] = T[(size_t)i * mv + q];
-  check_cuda(cudaMemcpyAsync(c->Yd, c->Yh, sizeof(double) * mv * k, cudaMemcpyHostToDevice, s), "h2d");
+  upload_y(c, mv, k);
   launch_ritz(c->vt, n, c->V, c->ldv, mv, k, c->Yd, c->AX64, s);
   c->n_launches += 3 + (k + 3) / 4;
   for (int i = 0; i < k; i += 4) {
@@ -653,7 +668,7 @@ int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* label
     K = std::min({K, m - B, mv});
     for (int i = 0; i < K; ++i)
       for (int q = 0; q < mv; ++q) c->Yh[(size_t)i * mv + q] = T[(size_t)i * mv + q];
-    check_cuda(cudaMemcpyAsync(c->Yd, c->Yh, sizeof(double) * mv * K, cudaMemcpyHostToDevice, s), "h2d");
+    upload_y(c, mv, K);
     {
       cudaEvent_t ea = nullptr, eb = nullptr;
       if (c->opts.profile) {

@@ -115,12 +115,12 @@ int orth_max_grid(VecType vt, int B, int threads);
 // V[:, 0:K] = V[:, 0:m] Y (Y: m x K column-major FP64 on device), then V[:, K:K+B] = V[:, m:m+B].
 // V is stored as ldv/4 panels of n x 4 (panel p = columns 4p..4p+3).
 // Q (n x 4 row-major) receives the carried block too.
-void launch_restart(VecType vt, int n, void* V, int64_t ldv, int m, int K, int B, const double* Y, void* Q,
+void launch_restart(VecType vt, int n, void* V, int64_t ldv, int m, int K, int B, const void* Y, void* Q,
                     cudaStream_t s);
 // Fill V[:, 0:B] with a seeded pseudo-random block.
 void launch_random_block(VecType vt, int n, void* V, int64_t ldv, int B, uint64_t seed, cudaStream_t s);
 // X64 = V[:, 0:m] Y (Y: m x k column-major FP64), X64 n x k column-major FP64; V unchanged.
-void launch_ritz(VecType vt, int n, const void* V, int64_t ldv, int m, int k, const double* Y, double* X64,
+void launch_ritz(VecType vt, int n, const void* V, int64_t ldv, int m, int k, const void* Y, double* X64,
                  cudaStream_t s);
 // partial[b][c] = sum over block b's rows of (AX_c - lam_c X_c)^2.
 void launch_column_resid(int n, int k, const double* X, const double* AX, const double* lam, double* partial,

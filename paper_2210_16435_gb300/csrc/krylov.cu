@@ -35,7 +35,7 @@ __device__ __forceinline__ void lds4(const VT* p, VT (&x)[4]) {
 // mode 1: into X (column-major n x K, FP64).
 template <typename VT, int MODE>
 __global__ void __launch_bounds__(256) tile_gemm_kernel(int n, VT* V, int64_t ldv, int m, int K, int B,
-                                                        const double* __restrict__ Y, VT* Q, double* X) {
+                                                        const VT* __restrict__ Y, VT* Q, double* X) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int width = m + B;
   VT* Vt = reinterpret_cast<VT*>(sm);  // width x kTS (transposed tile)
@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(256) tile_gemm_kernel(int n, VT* V, int64_t ld
     __syncthreads();
     for (int i = t; i < m * 64; i += blockDim.x) {
       const int c = i / 64, kk = i % 64;
-      Ys[i] = kk < kc ? (VT)Y[(size_t)c + (size_t)(k0 + kk) * m] : VT(0);
+      Ys[i] = kk < kc ? Y[(size_t)c + (size_t)(k0 + kk) * m] : VT(0);
     }
     __syncthreads();
     VT acc[4][4];
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(256) tile_gemm_kernel(int n, VT* V, int64_t ld
 }
 
 template <typename VT, int MODE>
-static void tile_gemm_launch(int n, VT* V, int64_t ldv, int m, int K, int B, const double* Y, VT* Q, double* X,
+static void tile_gemm_launch(int n, VT* V, int64_t ldv, int m, int K, int B, const VT* Y, VT* Q, double* X,
                              cudaStream_t s) {
   const size_t smem = sizeof(VT) * ((size_t)(m + B) * kTS + (size_t)m * 64);
   if (smem > 227 * 1024) fail(SFAIRSC_ERR_UNSUPPORTED, "Krylov basis too wide for the restart tile in this precision");
@@ -108,16 +108,17 @@ static void tile_gemm_launch(int n, VT* V, int64_t ldv, int m, int K, int B, con
   check_cuda(cudaGetLastError(), "tile gemm launch");
 }
 
-void launch_restart(VecType vt, int n, void* V, int64_t ldv, int m, int K, int B, const double* Y, void* Q,
+void launch_restart(VecType vt, int n, void* V, int64_t ldv, int m, int K, int B, const void* Y, void* Q,
                     cudaStream_t s) {
-  if (vt == VecType::F64) tile_gemm_launch<double, 0>(n, (double*)V, ldv, m, K, B, Y, (double*)Q, nullptr, s);
-  else tile_gemm_launch<float, 0>(n, (float*)V, ldv, m, K, B, Y, (float*)Q, nullptr, s);
+  if (vt == VecType::F64)
+    tile_gemm_launch<double, 0>(n, (double*)V, ldv, m, K, B, (const double*)Y, (double*)Q, nullptr, s);
+  else tile_gemm_launch<float, 0>(n, (float*)V, ldv, m, K, B, (const float*)Y, (float*)Q, nullptr, s);
 }
 
-void launch_ritz(VecType vt, int n, const void* V, int64_t ldv, int m, int k, const double* Y, double* X64,
+void launch_ritz(VecType vt, int n, const void* V, int64_t ldv, int m, int k, const void* Y, double* X64,
                  cudaStream_t s) {
-  if (vt == VecType::F64) tile_gemm_launch<double, 1>(n, (double*)V, ldv, m, k, 0, Y, nullptr, X64, s);
-  else tile_gemm_launch<float, 1>(n, (float*)V, ldv, m, k, 0, Y, nullptr, X64, s);
+  if (vt == VecType::F64) tile_gemm_launch<double, 1>(n, (double*)V, ldv, m, k, 0, (const double*)Y, nullptr, X64, s);
+  else tile_gemm_launch<float, 1>(n, (float*)V, ldv, m, k, 0, (const float*)Y, nullptr, X64, s);
 }
 
 __global__ void column_resid_kernel(int n, int k, const double* __restrict__ X, const double* __restrict__ AX,
