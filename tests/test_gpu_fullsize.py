@@ -1,0 +1,81 @@
+"""The bench configurations at full size, checked through the oracle.
+
+At n = 1,000,000 the oracle cannot solve the eigenproblem in a test's time,
+so the returned pairs are checked with properties that hold at any size,
+using the oracle's FP64 operator (Sec. 3.4 (i)): every residual
+||L_n^sigma x - lambda x|| <= 1e-6 sigma, F^T H = 0, H^T D H = I, lambda_1 = 0
+(Sec. 3.3: D^{1/2} 1 spans the null space of L_n inside null(C^T)), and the
+eigenvalues ascending.  The 256-graph batch is checked the same way for every
+graph, and against the oracle's dense solve on a sample of its graphs.
+"""
+import numpy as np
+import pytest
+import torch
+
+from msbm import configs
+from oracle import fairsc, problem
+from oracle.sfairsc import operator_from_graph, residual_norms
+
+pytestmark = pytest.mark.gpu
+
+
+def check_pairs(g, lam, H, tol_res=1e-6, tol_inv=1e-5):
+    W = g.to_scipy()
+    op = operator_from_graph(g)
+    d = problem.degrees(W)
+    X = H * np.sqrt(d)[:, None]
+    res = residual_norms(op, lam, X)
+    assert res.max() <= tol_res * op.sigma * 1.01, res.max() / op.sigma
+    if g.h > 1:
+        _, F, _ = problem.fairness_constraints(g.groups, g.h)
+        assert np.abs(F.T @ H).max() <= tol_inv * np.abs(H).sum(axis=0).max()
+    G = (H.T * d) @ H
+    assert np.abs(G - np.eye(H.shape[1])).max() <= tol_inv
+    assert abs(lam[0]) <= 1e-6 * op.sigma
+    assert np.all(np.diff(lam) >= -1e-6 * op.sigma)
+    return op
+
+
+def test_bench_workload_n1m_k50(built_lib):
+    """m-SBM n = 1M, k = 50, h = 10, BF16 weights, MIXED precision, block 4 (the bench's launch configuration)."""
+    from paper_2210_16435_gb300.solver import FairSC
+
+    c = configs.msbm_n1m_k50_h10()
+    g = c["graph"]
+    T = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    s = FairSC(T(g.row_ptr, torch.int32), T(g.col_idx, torch.int32), T(g.values, torch.bfloat16),
+               T(g.groups, torch.int32), k=c["k"], h=c["h"], prec="mixed", block=4)
+    lam, H, lab, info = s.solve()
+    s.close()
+    lam, H, lab = lam.cpu().numpy(), H.cpu().numpy(), lab.cpu().numpy()
+    op = check_pairs(g, lam, H)
+    assert info["max_resid"] <= 1e-6
+    assert abs(info["sigma"] - op.sigma) <= 1e-12 * op.sigma
+    # k-means labels: a partition into at most k clusters, every row labelled
+    assert lab.min() >= 0 and lab.max() < c["k"]
+
+
+def test_batch256_full(built_lib):
+    """The 256-graph batch at full size: every graph converges and passes the residual and invariant checks."""
+    from paper_2210_16435_gb300.solver import FairSCBatch
+
+    c = configs.msbm_batch256()
+    T = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    ents = [{"row_ptr": T(x["graph"].row_ptr, torch.int32), "col_idx": T(x["graph"].col_idx, torch.int32),
+             "values": T(x["graph"].values, torch.float32), "groups": T(x["graph"].groups, torch.int32),
+             "k": x["k"], "h": x["h"]} for x in c["graphs"]]
+    b = FairSCBatch(ents)
+    status, info = b.solve()
+    lams = [x.cpu().numpy() for x in b.lam]
+    Hs = [x.cpu().numpy() for x in b.H]
+    b.close()
+    assert status == [0] * len(ents), status
+    for x, lam, H in zip(c["graphs"], lams, Hs):
+        check_pairs(x["graph"], lam, H)
+    # against the oracle's dense solve (Algorithm 2 / eq. asigma) on the smallest graphs
+    small = sorted(range(len(ents)), key=lambda i: c["graphs"][i]["graph"].n)[:4]
+    for i in small:
+        g, k = c["graphs"][i]["graph"], c["graphs"][i]["k"]
+        lref, _, _, _, _ = fairsc.sfairsc_dense(g.to_scipy(), g.groups, g.h, k)
+        sigma = operator_from_graph(g).sigma
+        assert np.abs(lams[i] - lref[:k]).max() <= 1e-6 * sigma
