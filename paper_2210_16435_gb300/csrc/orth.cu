@@ -11,13 +11,16 @@
 //
 // One cooperative launch; each CTA owns a contiguous row range.  The basis
 // is stored as 4-column panels (panel p holds columns 4p..4p+3 as an n x 4
-// row-major array), so 32 consecutive rows of a panel are one contiguous
-// 16-byte-per-row run.  A warp takes 32-row blocks in two phases:
-//   phase A, one lane per row: load the row's panels (coalesced 512-byte
-//     warp loads), subtract V c (coefficients broadcast from shared memory),
-//     store the row, add its Gram entries;
-//   phase B, LPR lanes per row, lane p holding panel p: add the row's
-//     products to the new coefficients V^T u (the panels come back from L1/L2).
+// row-major array), so consecutive rows of a panel are one contiguous run.
+// A sweep streams the CTA's rows as slices of SR rows of every panel and of
+// U: each warp copies its next slice into its own shared-memory buffer with
+// cp.async while it works on the current one (no CTA barrier inside a sweep),
+// and treats each slice in two phases:
+//   phase A, LPA lanes per row: subtract V c from the row of U (coefficients
+//     broadcast from shared memory), store it, add its Gram entries;
+//   phase B, LPR lanes per row, lane p holding panel p: add the rows'
+//     products to the new coefficients V^T u.
+// Both phases read the panels from the slice, so V leaves HBM once per sweep.
 // FP32 path: inner products in FP32 windows carried by TwoSum and combined
 // over lanes by a TwoSum tree, then in FP64 over warps and CTAs in a fixed
 // order (bitwise reproducible).  FP64 path: FP64 throughout.
@@ -103,41 +106,110 @@ __device__ __forceinline__ int lanes_for(int np) {
   return np <= 1 ? 1 : np <= 2 ? 2 : np <= 4 ? 4 : np <= 8 ? 8 : np <= 16 ? 16 : 32;
 }
 
-// CTA b owns pairs p = b, b + grid, ...; sums partial[i][p] over CTAs i in
-// a fixed order and writes out[p].  Ends with __syncthreads.
-__device__ __forceinline__ void reduce_owned(const double* partial, int stride, int P, double* out, double* scratch) {
+// Fixed-order sums over the rows of the partials (row i, one per CTA, starts
+// at partial + i * stride).
+// The rows are cut into nch contiguous chunks, each summed by its own thread
+// with several loads in flight, and the chunk sums are added in a fixed
+// pairwise tree in shared memory.  The shape depends only on the row count
+// and the number of values, so every CTA that forms a value forms the same bits.
+__device__ __forceinline__ int chunk_count(int per_row) {
+  int nch = 1;
+  while (nch < 256 && 2 * nch * per_row <= kOT) nch *= 2;
+  return nch;
+}
+
+// Pairwise tree over the nch chunk sums held at scratch[(c * cnt + q) * w + e]
+// (c < nch, q < cnt, e < w); leaves the totals in chunk 0.  Every thread of
+// the CTA calls it.
+__device__ __forceinline__ void chunk_tree(double* scratch, int nch, int cnt, int w) {
+  const int t = threadIdx.x, q = t % cnt, c = t / cnt;
+  __syncthreads();
+  for (int h = nch >> 1; h >= 1; h >>= 1) {
+    if (c < h)
+      for (int e = 0; e < w; ++e) scratch[(c * cnt + q) * w + e] += scratch[((c + h) * cnt + q) * w + e];
+    __syncthreads();
+  }
+}
+
+// CTA b owns coefficients p = b, b + grid, ...; writes out[p] = sum over rows
+// i < nrows of partial[i][p].  Ends with __syncthreads.
+__device__ __forceinline__ void reduce_owned(const double* partial, int stride, int nrows, int P, double* out,
+                                             double* scratch) {
   const int nct = gridDim.x;
   const int Q = P > (int)blockIdx.x ? (P - (int)blockIdx.x + nct - 1) / nct : 0;
   if (Q == 0) {
     __syncthreads();
     return;
   }
-  const int T = blockDim.x;
-  const int nchunk = max(1, min(nct, T / Q));
+  const int nch = chunk_count(Q);
   const int t = threadIdx.x, q = t % Q, c = t / Q;
-  const int p = blockIdx.x + q * nct;
-  if (c < nchunk) {
-    const int lo = (int)((long long)c * nct / nchunk), hi = (int)((long long)(c + 1) * nct / nchunk);
-    double s = 0.0;
-    for (int i = lo; i < hi; ++i) s += __ldcg(partial + (size_t)i * stride + p);
-    scratch[c * Q + q] = s;
+  if (c < nch) {
+    const int lo = (int)((long long)c * nrows / nch), hi = (int)((long long)(c + 1) * nrows / nch);
+    const double* src = partial + blockIdx.x + (size_t)q * nct;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    int i = lo;
+    for (; i + 4 <= hi; i += 4) {
+      double x[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) x[e] = __ldcg(src + (size_t)(i + e) * stride);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) s[e] += x[e];
+    }
+    for (; i < hi; ++i) s[0] += __ldcg(src + (size_t)i * stride);
+    scratch[c * Q + q] = (s[0] + s[1]) + (s[2] + s[3]);
   }
-  __syncthreads();
-  if (t < Q) {
-    double s = 0.0;
-    for (int cc = 0; cc < nchunk; ++cc) s += scratch[cc * Q + t];
-    out[blockIdx.x + t * nct] = s;
-  }
+  chunk_tree(scratch, nch, Q, 1);
+  if (t < Q) out[blockIdx.x + t * nct] = scratch[t];
   __syncthreads();
 }
 
-// All CTAs: out[t] = sum over CTAs of partial[i][off + t], t < cnt (fixed order).
-__device__ __forceinline__ void reduce_all(const double* partial, int stride, int off, int cnt, double* out) {
-  if ((int)threadIdx.x < cnt) {
-    double s = 0.0;
-    for (int i = 0; i < (int)gridDim.x; ++i) s += __ldcg(partial + (size_t)i * stride + off + threadIdx.x);
-    out[threadIdx.x] = s;
+// All CTAs: out[t] = sum over rows i < nrows of partial[i][off + t], t < cnt
+// (cnt <= 16; off even).  Ends with __syncthreads.
+__device__ __forceinline__ void reduce_all(const double* partial, int stride, int nrows, int off, int cnt, double* out,
+                                           double* scratch) {
+  const int w = (cnt & 1) ? 1 : 2;  // values per load
+  const int nl = cnt / w;           // loads per row
+  const int nch = chunk_count(nl);
+  const int t = threadIdx.x, q = t % nl, c = t / nl;
+  if (c < nch) {
+    const int lo = (int)((long long)c * nrows / nch), hi = (int)((long long)(c + 1) * nrows / nch);
+    double s[4][2] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
+    if (w == 2) {
+      const double2* src = reinterpret_cast<const double2*>(partial + off) + q;
+      const int st2 = stride / 2;
+      int i = lo;
+      for (; i + 4 <= hi; i += 4) {
+        double2 x[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) x[e] = __ldcg(src + (size_t)(i + e) * st2);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          s[e][0] += x[e].x;
+          s[e][1] += x[e].y;
+        }
+      }
+      for (; i < hi; ++i) {
+        const double2 x = __ldcg(src + (size_t)i * st2);
+        s[0][0] += x.x;
+        s[0][1] += x.y;
+      }
+    } else {
+      const double* src = partial + off + q;
+      int i = lo;
+      for (; i + 4 <= hi; i += 4) {
+        double x[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) x[e] = __ldcg(src + (size_t)(i + e) * stride);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) s[e][0] += x[e];
+      }
+      for (; i < hi; ++i) s[0][0] += __ldcg(src + (size_t)i * stride);
+    }
+    for (int e = 0; e < w; ++e) scratch[(c * nl + q) * w + e] = (s[0][e] + s[1][e]) + (s[2][e] + s[3][e]);
   }
+  chunk_tree(scratch, nch, nl, w);
+  if (t < nl)
+    for (int e = 0; e < w; ++e) out[t * w + e] = scratch[t * w + e];
   __syncthreads();
 }
 
@@ -161,24 +233,62 @@ struct OrthArgs {
   int J, j;
 };
 
-// Shared memory: coefficients (kCoefMax VT), per-warp partials (kOW x
-// red_stride doubles), reduction scratch (1024 doubles), per-warp updated rows
-// (kOW x 32 x 4 VT).  Kept small so that L1 holds the panels phase B re-reads.
+// Sweep slices: SR consecutive rows of every panel V[:, 4p:4p+4] (p < np)
+// and of U, copied by the warp that will use them into its own shared-memory
+// buffer with cp.async (16 bytes per lane, zero fill past the CTA's rows),
+// two buffers per warp so the next slice is in flight while one is used.  A
+// slice is row-major: row i holds the row's np panel entries and then its row
+// of U, rsc 16-byte chunks apart, rsc padded so that the lanes of a quarter
+// warp reading different rows fall in different banks.
+constexpr int kWarpBuf = 13312;  // bytes of slice buffer per warp (two slices)
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+  const unsigned n = valid ? 16u : 0u;  // src-size 0 fills the 16 bytes with zeros
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(smem)), "l"(gmem), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Slice geometry for np panels: rows per slice, lanes per row in phase A, and
+// the row stride in 16-byte chunks.
+struct SliceShape {
+  int sr, lpa, rsc;
+};
+template <typename VT>
+__host__ __device__ inline SliceShape slice_shape(int np) {
+  constexpr int ch = (int)sizeof(VT) / 4;  // 16-byte chunks per panel row
+  for (int sr = 16; sr >= 2; sr >>= 1) {
+    const int lpa = 32 / sr;
+    int rsc = (np + 1) * ch;
+    if (ch == 1)
+      while ((rsc & 7) != (lpa & 7)) ++rsc;
+    else
+      rsc |= 1;
+    if (2 * sr * rsc * 16 <= kWarpBuf) return SliceShape{sr, lpa, rsc};
+  }
+  return SliceShape{0, 0, 0};
+}
+
+// Shared memory: the slice buffers (kOW x kWarpBuf; between sweeps the
+// per-warp partials, kOW x red_stride doubles, reuse them), the coefficients
+// (kCoefMax VT) and the reduction scratch (1024 doubles).
 template <typename VT, int NC>
 constexpr size_t orth_smem_bytes() {
-  return sizeof(VT) * kCoefMax + sizeof(double) * ((size_t)kOW * red_stride<NC>() + 1024) + sizeof(VT) * kOW * 32 * 4 +
-         256;
+  return (size_t)kOW * kWarpBuf + sizeof(VT) * kCoefMax + sizeof(double) * 1024 + 128;
 }
+static_assert(sizeof(double) * kOW * (1024 + 16) <= (size_t)kOW * kWarpBuf, "per-warp partials fit in the slice buffers");
 
 template <typename VT, int B, int NC>
 __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  VT* cfs = reinterpret_cast<VT*>(smraw);                                  // coefficients c*B + v
+  extern __shared__ __align__(128) unsigned char smraw[];
   constexpr int kRed = red_stride<NC>();
-  constexpr int kXo = kRed - 16;                                           // extras offset
-  double* red = reinterpret_cast<double*>(smraw + sizeof(VT) * kCoefMax);  // kOW x kRed
-  double* scratch = red + (size_t)kOW * kRed;                              // 1024
-  VT* uws = reinterpret_cast<VT*>(scratch + 1024);                         // kOW x 32 x 4
+  constexpr int kXo = kRed - 16;                                                      // extras offset
+  double* red = reinterpret_cast<double*>(smraw);                                     // kOW x kRed, between sweeps
+  VT* cfs = reinterpret_cast<VT*>(smraw + (size_t)kOW * kWarpBuf);                    // coefficients c*B + v
+  double* scratch = reinterpret_cast<double*>(smraw + (size_t)kOW * kWarpBuf + sizeof(VT) * kCoefMax);
   __shared__ double gram_s[16], R1[16], R2[16], Rd1[16], Rd2[16], unorm[4];
   __shared__ int brk, again;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -189,21 +299,48 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
   constexpr int NG = B * (B + 1) / 2;  // unique Gram entries
   constexpr int NA = NG > B ? NG : B;
   VT* U = a.U;
-  VT* uw = uws + (size_t)warp * 32 * 4;
+  unsigned char* wbuf = smraw + (size_t)warp * kWarpBuf;  // this warp's two slices
   if (threadIdx.x == 0) brk = 0;
   __syncthreads();
 
   // sweep kinds: 0 = coefficients + input norms; 1 = update with a.coef, then the
   // next coefficients and the Gram matrix; 2 = update with a.coef, then the Gram matrix.
-  auto sweep = [&](int kind) {
+  // A warp takes the slices r0 + (warp + kOW k) SR, each in two phases:
+  //   phase A, LPA lanes per row, lane g summing panels g, g + LPA, ...:
+  //     u <- u - V c, written back to the slice and to U, Gram entries;
+  //   phase B, LPR lanes per row, lane p0 (+32 q) holding panel p0 (+32 q):
+  //     the new coefficients V^T u.
+  auto sweep = [&](int kind) -> bool {
     const bool upd = kind >= 1, want_c = kind <= 1;
-    if (upd) {
+    if (upd)
       for (int i = threadIdx.x; i < P; i += blockDim.x) cfs[i] = (VT)__ldcg(a.coef + i);
-      __syncthreads();
-    }
+    __syncthreads();  // coefficients in place; the slice buffers are free
+    constexpr int CH = (int)sizeof(VT) / 4;
+    const SliceShape sh = slice_shape<VT>(np);
+    const int SR = sh.sr, LPA = sh.lpa, rsc = sh.rsc;
+    const int sbytes = SR * rsc * 16;  // one slice
     const int LPR = NC == 1 ? lanes_for(np) : 32;
     const int RPW = 32 / LPR;
     const int p0 = lane & (LPR - 1), ri = lane / LPR;
+    const int nsl = (r1 - r0 + SR - 1) / SR;  // slices of this CTA
+    const int ncols = (np + 1) * CH;          // chunks per row to copy
+    // copy slice k of this warp into buffer k & 1 (one commit group, possibly empty)
+    auto fetch = [&](int k) {
+      const int sl = warp + kOW * k;
+      if (sl < nsl) {
+        const int rb = r0 + sl * SR;
+        unsigned char* dst = wbuf + (k & 1) * sbytes;
+        for (int idx = lane; idx < SR * ncols; idx += 32) {
+          const int i = idx % SR, c = idx / SR;  // lanes run down a column: coalesced rows
+          const int col = c / CH, part = c % CH;
+          const bool valid = rb + i < r1;
+          const int row = valid ? rb + i : r0;
+          const VT* src = (col < np ? a.V + col * pn : U) + (size_t)row * 4 + part * (4 / CH);
+          cp_async16(dst + ((size_t)i * rsc + c) * 16, src, valid);
+        }
+      }
+      cp_async_commit();
+    };
     Acc<VT> acc[NC][4][B];
     Acc<VT> ga[NA];
 #pragma unroll
@@ -214,91 +351,99 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
         for (int v = 0; v < B; ++v) acc[q][jj][v].zero();
 #pragma unroll
     for (int e = 0; e < NA; ++e) ga[e].zero();
-    int nb = 0;
-    for (int rb = r0 + warp * 32; rb < r1; rb += kOW * 32) {
-      // ---- phase A: lane = row
-      const int r = rb + lane;
-      VT u[4] = {VT(0), VT(0), VT(0), VT(0)};
-      if (r < r1) {
-        ld4(U + (size_t)r * 4, u);
-        if (upd) {
-          VT d[B];
+    fetch(0);
+    for (int k = 0; warp + kOW * k < nsl; ++k) {
+      fetch(k + 1);
+      cp_async_wait<1>();
+      __syncwarp();
+      const int rb = r0 + (warp + kOW * k) * SR;
+      const int rows = min(SR, r1 - rb);
+      const unsigned char* sl = wbuf + (k & 1) * sbytes;
+      auto at = [&](int i, int col) { return reinterpret_cast<const VT*>(sl + ((size_t)i * rsc + col * CH) * 16); };
+      // ---- phase A
+      {
+        const int i = lane / LPA, g = lane & (LPA - 1);
+        VT d[B];
 #pragma unroll
-          for (int v = 0; v < B; ++v) d[v] = VT(0);
+        for (int v = 0; v < B; ++v) d[v] = VT(0);
+        if (upd) {
           const int nfull = J >> 2;  // panels whose 4 columns are all < J
-#pragma unroll 8
-          for (int pp = 0; pp < nfull; ++pp) {
+          for (int pp = g; pp < nfull; pp += LPA) {
             VT x[4];
-            ld4(a.V + pp * pn + (size_t)r * 4, x);
+            ld4(at(i, pp), x);
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj)
 #pragma unroll
               for (int v = 0; v < B; ++v) d[v] = fma(x[jj], cfs[(4 * pp + jj) * B + v], d[v]);
           }
-          if (nfull < np) {
+          if (nfull < np && (nfull & (LPA - 1)) == g) {
             VT x[4];
-            ld4(a.V + nfull * pn + (size_t)r * 4, x);
+            ld4(at(i, nfull), x);
             for (int jj = 0; jj < (J & 3); ++jj)
 #pragma unroll
               for (int v = 0; v < B; ++v) d[v] = fma(x[jj], cfs[(4 * nfull + jj) * B + v], d[v]);
           }
+          for (int o = 1; o < LPA; o <<= 1)
 #pragma unroll
-          for (int v = 0; v < B; ++v) u[v] -= d[v];
-          st4(U + (size_t)r * 4, u);
-        } else {
-          for (int pp = 0; pp < np; ++pp) asm volatile("prefetch.global.L1 [%0];" ::"l"(a.V + pp * pn + (size_t)r * 4));
+            for (int v = 0; v < B; ++v) d[v] += __shfl_xor_sync(0xffffffffu, d[v], o);
+        }
+        if (g == 0 && i < rows) {
+          VT u[4];
+          ld4(at(i, np), u);
+          if (upd) {
+#pragma unroll
+            for (int v = 0; v < B; ++v) u[v] -= d[v];
+            st4(const_cast<VT*>(at(i, np)), u);
+            st4(U + (size_t)(rb + i) * 4, u);
+          }
+          if (kind == 0) {
+#pragma unroll
+            for (int v = 0; v < B; ++v) ga[v].fma_(u[v], u[v]);
+          } else {
+            int e = 0;
+#pragma unroll
+            for (int v = 0; v < B; ++v)
+#pragma unroll
+              for (int w2 = v; w2 < B; ++w2) ga[e++].fma_(u[v], u[w2]);
+          }
         }
       }
-      if (kind == 0) {
-#pragma unroll
-        for (int v = 0; v < B; ++v) ga[v].fma_(u[v], u[v]);
-      } else {
-        int e = 0;
-#pragma unroll
-        for (int v = 0; v < B; ++v)
-#pragma unroll
-          for (int w2 = v; w2 < B; ++w2) ga[e++].fma_(u[v], u[w2]);
-      }
-      if (want_c) st4(uw + lane * 4, u);
       __syncwarp();
-      // ---- phase B: LPR lanes per row, lane p0 (+32 q) holding panel p0 (+32 q)
+      // ---- phase B (rows past the CTA's end are zero in the slice)
       if (want_c) {
-        const int nrow = min(32, r1 - rb);
-        for (int s0 = 0; s0 < LPR; s0 += 4) {
-          // four rows' loads in flight before their products
-          VT xs[4][NC][4], us[4][4];
+        for (int s0 = 0; s0 < SR; s0 += 2 * RPW) {
+          VT xs[2][NC][4], us[2][4];
 #pragma unroll
-          for (int t = 0; t < 4; ++t) {
-            const int i = ri + RPW * (s0 + t);
-            const bool in = s0 + t < LPR && i < nrow;
-            if (in) ld4(uw + i * 4, us[t]);
-            else us[t][0] = us[t][1] = us[t][2] = us[t][3] = VT(0);
+          for (int tt = 0; tt < 2; ++tt) {
+            const int i = s0 + ri + RPW * tt;
+            const bool in = i < SR;
+            if (in) ld4(at(i, np), us[tt]);
+            else us[tt][0] = us[tt][1] = us[tt][2] = us[tt][3] = VT(0);
 #pragma unroll
             for (int q = 0; q < NC; ++q) {
               const int pp = p0 + 32 * q;
               if (in && pp < np) {
-                ld4(a.V + pp * pn + (size_t)(rb + i) * 4, xs[t][q]);
+                ld4(at(i, pp), xs[tt][q]);
                 if (4 * pp + 4 > J)
 #pragma unroll
                   for (int jj = 0; jj < 4; ++jj)
-                    if (4 * pp + jj >= J) xs[t][q][jj] = VT(0);
+                    if (4 * pp + jj >= J) xs[tt][q][jj] = VT(0);
               } else {
-                xs[t][q][0] = xs[t][q][1] = xs[t][q][2] = xs[t][q][3] = VT(0);
+                xs[tt][q][0] = xs[tt][q][1] = xs[tt][q][2] = xs[tt][q][3] = VT(0);
               }
             }
           }
 #pragma unroll
-          for (int t = 0; t < 4; ++t)
+          for (int tt = 0; tt < 2; ++tt)
 #pragma unroll
             for (int q = 0; q < NC; ++q)
 #pragma unroll
               for (int jj = 0; jj < 4; ++jj)
 #pragma unroll
-                for (int v = 0; v < B; ++v) acc[q][jj][v].fma_(xs[t][q][jj], us[t][v]);
+                for (int v = 0; v < B; ++v) acc[q][jj][v].fma_(xs[tt][q][jj], us[tt][v]);
         }
       }
-      __syncwarp();
-      if (++nb == 4) {
+      if ((k & 3) == 3) {
 #pragma unroll
         for (int q = 0; q < NC; ++q)
 #pragma unroll
@@ -307,9 +452,11 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
             for (int v = 0; v < B; ++v) acc[q][jj][v].flush();
 #pragma unroll
         for (int e = 0; e < NA; ++e) ga[e].flush();
-        nb = 0;
       }
+      __syncwarp();  // the buffer is free for slice k + 2
     }
+    cp_async_wait<0>();
+    __syncthreads();  // every warp is done with its slices: the buffers take the partials
     // ---- combine over the warp's lanes, then over warps into this CTA's partial
 #pragma unroll
     for (int q = 0; q < NC; ++q)
@@ -360,38 +507,50 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
       for (int w = 0; w < kOW; ++w) s += red[(size_t)w * kRed + kXo + threadIdx.x];
       a.partial[(size_t)blockIdx.x * kStride + (kind == 0 ? kNormOff : kGramOff) + threadIdx.x] = s;
     }
+    return true;
   };
 
-  // Thread-per-row Gram of U (B x B) to partial[off..], optionally after U <- U R1^{-1}.
+  // Thread-per-row Gram of U (B x B) over this CTA's rows to partial[off..],
+  // optionally after U <- U R1^{-1}; four rows per thread in flight.
   auto gram_rows = [&](int off, bool apply_r1) {
     Acc<VT> g[NG];
 #pragma unroll
     for (int e = 0; e < NG; ++e) g[e].zero();
-    int nb = 0;
-    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-      VT u[4];
-      ld4(U + (size_t)r * 4, u);
-      if (apply_r1) {
+    auto rows = [&](int lo, int hi) {
+      int nb = 0;
+      for (int rb = lo + threadIdx.x; rb < hi; rb += 4 * kOT) {
+        VT u[4][4];
 #pragma unroll
-        for (int v = 0; v < B; ++v) {
-          VT s = u[v];
-#pragma unroll
-          for (int q = 0; q < v; ++q) s -= u[q] * (VT)Rd1[q * B + v];
-          u[v] = s / (VT)Rd1[v * B + v];
+        for (int t = 0; t < 4; ++t) {
+          if (rb + t * kOT < hi) ld4(U + (size_t)(rb + t * kOT) * 4, u[t]);
+          else u[t][0] = u[t][1] = u[t][2] = u[t][3] = VT(0);
         }
-        st4(U + (size_t)r * 4, u);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          if (apply_r1) {
+#pragma unroll
+            for (int v = 0; v < B; ++v) {
+              VT s = u[t][v];
+#pragma unroll
+              for (int q = 0; q < v; ++q) s -= u[t][q] * (VT)Rd1[q * B + v];
+              u[t][v] = s / (VT)Rd1[v * B + v];
+            }
+            if (rb + t * kOT < hi) st4(U + (size_t)(rb + t * kOT) * 4, u[t]);
+          }
+          int e = 0;
+#pragma unroll
+          for (int v = 0; v < B; ++v)
+#pragma unroll
+            for (int w2 = v; w2 < B; ++w2) g[e++].fma_(u[t][v], u[t][w2]);
+        }
+        if (++nb == 4) {
+#pragma unroll
+          for (int ee = 0; ee < NG; ++ee) g[ee].flush();
+          nb = 0;
+        }
       }
-      int e = 0;
-#pragma unroll
-      for (int v = 0; v < B; ++v)
-#pragma unroll
-        for (int w2 = v; w2 < B; ++w2) g[e++].fma_(u[v], u[w2]);
-      if (++nb == 16) {
-#pragma unroll
-        for (int ee = 0; ee < NG; ++ee) g[ee].flush();
-        nb = 0;
-      }
-    }
+    };
+    rows(r0, r1);
 #pragma unroll
     for (int e = 0; e < NG; ++e) g[e].reduce(1);
     __syncthreads();
@@ -448,19 +607,19 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
   int sweeps = 0;
   if (J > 0) {
     // sweep 1: c1 = V^T U and the input norms
-    sweep(0);
+    if (!sweep(0)) return;
     ++sweeps;
     if (!grid_sync(a.bar, a.err)) return;
-    reduce_owned(a.partial, kStride, P, a.coef, scratch);
+    reduce_owned(a.partial, kStride, gridDim.x, P, a.coef, scratch);
     if (a.j >= 0)
       for (int p = blockIdx.x; p < P; p += gridDim.x) a.H[(size_t)(p / B) + (size_t)a.ldh * (a.j + p % B)] = a.coef[p];
-    reduce_all(a.partial, kStride, kNormOff, B, unorm);
+    reduce_all(a.partial, kStride, gridDim.x, kNormOff, B, unorm, scratch);
     if (!grid_sync(a.bar, a.err)) return;
     // sweep 2: U -= V c1; c2 = V^T U; Gram
-    sweep(1);
+    if (!sweep(1)) return;
     ++sweeps;
     if (!grid_sync(a.bar, a.err)) return;
-    reduce_all(a.partial, kStride, kGramOff, B * B, gram_s);
+    reduce_all(a.partial, kStride, gridDim.x, kGramOff, B * B, gram_s, scratch);
     if (threadIdx.x == 0) {
       again = 0;
       for (int v = 0; v < B; ++v)
@@ -468,21 +627,21 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
     }
     __syncthreads();
     if (again) {
-      reduce_owned(a.partial, kStride, P, a.coef, scratch);
+      reduce_owned(a.partial, kStride, gridDim.x, P, a.coef, scratch);
       if (a.j >= 0)
         for (int p = blockIdx.x; p < P; p += gridDim.x) a.H[(size_t)(p / B) + (size_t)a.ldh * (a.j + p % B)] += a.coef[p];
       if (!grid_sync(a.bar, a.err)) return;
       // sweep 3: U -= V c2; Gram
-      sweep(2);
+      if (!sweep(2)) return;
       ++sweeps;
       if (!grid_sync(a.bar, a.err)) return;
-      reduce_all(a.partial, kStride, kGramOff, B * B, gram_s);
+      reduce_all(a.partial, kStride, gridDim.x, kGramOff, B * B, gram_s, scratch);
     }
   } else {
     if (threadIdx.x < B) unorm[threadIdx.x] = 0.0;
     gram_rows(kGramOff, false);
     if (!grid_sync(a.bar, a.err)) return;
-    reduce_all(a.partial, kStride, kGramOff, B * B, gram_s);
+    reduce_all(a.partial, kStride, gridDim.x, kGramOff, B * B, gram_s, scratch);
   }
   cholesky(R1, Rd1);
 
@@ -490,7 +649,7 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
     // Cholesky QR a second time: U <- U R1^{-1}, Gram again
     gram_rows(kGram2Off, true);
     if (!grid_sync(a.bar, a.err)) return;
-    reduce_all(a.partial, kStride, kGram2Off, B * B, gram_s);
+    reduce_all(a.partial, kStride, gridDim.x, kGram2Off, B * B, gram_s, scratch);
     if (threadIdx.x < B) unorm[threadIdx.x] = 0.0;
     __syncthreads();
     cholesky(R2, Rd2);
@@ -501,30 +660,39 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
     }
     __syncthreads();
   }
-
   // V[:, J:J+B] = U R^{-1} (inside panel J/4: J % 4 + B <= 4) and its copy Q
   VT* Vp = a.V + (size_t)(J / 4) * pn;
   const int c0 = J & 3;
-  for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-    VT u[4];
-    ld4(U + (size_t)r * 4, u);
-    if (B > 1) {
+  auto final_rows = [&](int lo, int hi) {
+    for (int rb = lo + threadIdx.x; rb < hi; rb += 4 * kOT) {
+      VT u[4][4];
 #pragma unroll
-      for (int v = 0; v < B; ++v) {
-        VT s = u[v];
+      for (int t = 0; t < 4; ++t)
+        if (rb + t * kOT < hi) ld4(U + (size_t)(rb + t * kOT) * 4, u[t]);
 #pragma unroll
-        for (int q = 0; q < v; ++q) s -= u[q] * (VT)Rd2[q * B + v];
-        u[v] = s / (VT)Rd2[v * B + v];
+      for (int t = 0; t < 4; ++t) {
+        const int r = rb + t * kOT;
+        if (r >= hi) continue;
+        if (B > 1) {
+#pragma unroll
+          for (int v = 0; v < B; ++v) {
+            VT s = u[t][v];
+#pragma unroll
+            for (int q = 0; q < v; ++q) s -= u[t][q] * (VT)Rd2[q * B + v];
+            u[t][v] = s / (VT)Rd2[v * B + v];
+          }
+        } else {
+          u[t][0] = u[t][0] / (VT)Rd1[0];
+        }
+#pragma unroll
+        for (int v = 0; v < B; ++v) {
+          Vp[(size_t)r * 4 + c0 + v] = u[t][v];
+          a.Q[(size_t)r * 4 + v] = u[t][v];
+        }
       }
-    } else {
-      u[0] = u[0] / (VT)Rd1[0];
     }
-#pragma unroll
-    for (int v = 0; v < B; ++v) {
-      Vp[(size_t)r * 4 + c0 + v] = u[v];
-      a.Q[(size_t)r * 4 + v] = u[v];
-    }
-  }
+  };
+  final_rows(r0, r1);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (brk) {
       atomicOr(a.err, kErrBreakdown);
