@@ -332,11 +332,13 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   c->ytil = c->dalloc<unsigned char>((size_t)n * 4 * vs);
   c->ytil64 = c->dalloc<double>((size_t)n * 4);
   c->op_partial = c->dalloc<double>((size_t)grid * kMaxGroups * 4);
-  c->barrier = c->dalloc<unsigned>(8);
+  // words: [0..1] the operator's 64-bit barrier counter, [2] error word,
+  // [4..7] operator work counters, [8..9] the Gram-Schmidt kernel's counter
+  c->barrier = c->dalloc<unsigned>(16);
   c->err = c->barrier + 2;
   c->brk_step = c->dalloc<int>(1);
   c->sweeps = c->dalloc<int>(1);
-  check_cuda(cudaMemsetAsync(c->barrier, 0, 8 * sizeof(unsigned), s), "memset");
+  check_cuda(cudaMemsetAsync(c->barrier, 0, 16 * sizeof(unsigned), s), "memset");
   OpPlan& o = c->op;
   o.n = n;
   o.h = h;
@@ -361,7 +363,7 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   o.ytil = c->ytil;
   o.partial = c->op_partial;
   o.cta_rows = c->cta_rows;
-  o.barrier = c->barrier;
+  o.barrier = reinterpret_cast<unsigned long long*>(c->barrier);
   o.err = c->err;
   o.work = c->barrier + 4;
   c->op64 = o;
@@ -418,7 +420,7 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   q.partial = c->orth_partial;
   q.coef = c->orth_coef;
   q.cta_rows = c->cta_rows_orth;
-  q.barrier = c->barrier;
+  q.barrier = reinterpret_cast<unsigned long long*>(c->barrier + 8);
   q.err = c->err;
   q.brk_step = c->brk_step;
   q.sweeps = c->sweeps;
@@ -449,7 +451,7 @@ void check_err_word(sfairsc_ctx* c) {
   check_cuda(cudaMemcpyAsync(&e, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream), "d2h");
   check_cuda(cudaStreamSynchronize(c->stream), "sync");
   if (e) {
-    check_cuda(cudaMemsetAsync(c->barrier, 0, 4 * sizeof(unsigned), c->stream), "memset");
+    check_cuda(cudaMemsetAsync(c->barrier, 0, 16 * sizeof(unsigned), c->stream), "memset");
     check_cuda(cudaStreamSynchronize(c->stream), "sync");
     if (e & kErrBarrierTimeout) fail(SFAIRSC_ERR_DEVICE_TIMEOUT, "a grid barrier timed out");
   }

@@ -129,13 +129,18 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 }
 
 // ---------------------------------------------------------------- grid barrier
-// Sense-by-generation barrier over all CTAs of a cooperative launch.  The
-// spin is bounded: after `limit_ns` nanoseconds the waiting CTA sets
-// kErrBarrierTimeout in *err and the barrier returns false, so no launch can
-// hang.  Co-residency of all CTAs is guaranteed by the cooperative launch.
+// Barrier over all CTAs of a cooperative launch on one 64-bit arrival counter
+// that only grows: a CTA adds 1 and waits until the counter reaches the next
+// multiple of the grid size.  All CTAs of one barrier arrive before any CTA
+// can arrive at the next, so the arrivals of barrier i return values in
+// [i G, (i + 1) G) for grid size G.  A counter therefore serves every launch
+// of kernels with one grid size (each passes all of its barriers); it starts
+// at zero and is zeroed again after an error.  The spin is bounded: after
+// `limit_ns` nanoseconds the waiting CTA sets kErrBarrierTimeout in *err and
+// the barrier returns false, so no launch can hang.  Co-residency of all CTAs
+// is guaranteed by the cooperative launch.
 struct GridBarrier {
-  unsigned* count;       // arrivals in the current generation
-  unsigned* generation;  // incremented by the last arriver
+  unsigned long long* count;  // arrivals so far
 };
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
@@ -151,23 +156,28 @@ __device__ __forceinline__ unsigned atom_add_acqrel_gpu(unsigned* p, unsigned v)
   asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
   return old;
 }
+__device__ __forceinline__ unsigned long long ld_acquire_gpu_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long atom_add_acqrel_gpu_u64(unsigned long long* p, unsigned long long v) {
+  unsigned long long old;
+  asm volatile("atom.add.acq_rel.gpu.global.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+  return old;
+}
 
 __device__ __forceinline__ bool grid_sync(GridBarrier bar, unsigned* err, unsigned long long limit_ns = 2000000000ull) {
   __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    unsigned gen = ld_acquire_gpu(bar.generation);
-    __threadfence();
-    unsigned arrived = atom_add_acqrel_gpu(bar.count, 1u);
-    if (arrived == gridDim.x * gridDim.y * gridDim.z - 1) {
-      *bar.count = 0u;
-      __threadfence();
-      st_release_gpu(bar.generation, gen + 1u);
-    } else {
-      unsigned long long t0 = globaltimer_ns();
-      while (ld_acquire_gpu(bar.generation) == gen) {
-        __nanosleep(64);
+    const unsigned long long g = (unsigned long long)gridDim.x * gridDim.y * gridDim.z;
+    const unsigned long long old = atom_add_acqrel_gpu_u64(bar.count, 1ull);
+    const unsigned long long target = (old / g + 1ull) * g;
+    if (ld_acquire_gpu_u64(bar.count) < target) {
+      const unsigned long long t0 = globaltimer_ns();
+      while (ld_acquire_gpu_u64(bar.count) < target) {
         if (globaltimer_ns() - t0 > limit_ns) {
           atomicOr(err, kErrBarrierTimeout);
           ok = 0;

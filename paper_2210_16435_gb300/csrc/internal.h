@@ -63,7 +63,7 @@ struct OpPlan {
   void* ytil = nullptr;        // VT[n * 4]
   double* partial = nullptr;   // double[grid * 32 * 4]
   const int32_t* cta_rows = nullptr;  // int32[grid + 1]
-  unsigned* barrier = nullptr; // 2 words
+  unsigned long long* barrier = nullptr;  // grid barrier arrival counter (64-bit)
   unsigned* err = nullptr;
   unsigned* work = nullptr;    // 1 word: dynamic row-block counter of the SpMV
 };
@@ -102,7 +102,7 @@ struct OrthPlan {
   double* partial = nullptr;  // grid * (mmax + 4) * 4
   double* coef = nullptr;     // (mmax + 4) * 4 reduced coefficients
   const int32_t* cta_rows = nullptr;
-  unsigned* barrier = nullptr;
+  unsigned long long* barrier = nullptr;  // grid barrier arrival counter (64-bit)
   unsigned* err = nullptr;
   int* brk_step = nullptr;    // smallest step j whose new block lost rank (atomicMin)
   int* sweeps = nullptr;      // accumulates the number of passes over V

@@ -530,7 +530,7 @@ static void launch_t(const OpPlan& p, const void* w, int64_t wrs, int64_t wcs, v
   a.ytil = static_cast<VT*>(p.ytil);
   a.partial = p.partial;
   a.cta_rows = p.cta_rows;
-  a.bar = GridBarrier{p.barrier, p.barrier + 1};
+  a.bar = GridBarrier{p.barrier};
   a.err = p.err;
   a.work = p.work;
   const size_t smem = operator_smem_bytes(p.threads, p.h, B, sizeof(VT) == 8 ? VecType::F64 : VecType::F32);

@@ -516,6 +516,11 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
     Acc<VT> g[NG];
 #pragma unroll
     for (int e = 0; e < NG; ++e) g[e].zero();
+    VT rd[B][B];  // R1 in the row type, converted once
+#pragma unroll
+    for (int q = 0; q < B; ++q)
+#pragma unroll
+      for (int v = 0; v < B; ++v) rd[q][v] = (VT)Rd1[q * B + v];
     auto rows = [&](int lo, int hi) {
       int nb = 0;
       for (int rb = lo + threadIdx.x; rb < hi; rb += 4 * kOT) {
@@ -532,8 +537,8 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
             for (int v = 0; v < B; ++v) {
               VT s = u[t][v];
 #pragma unroll
-              for (int q = 0; q < v; ++q) s -= u[t][q] * (VT)Rd1[q * B + v];
-              u[t][v] = s / (VT)Rd1[v * B + v];
+              for (int q = 0; q < v; ++q) s -= u[t][q] * rd[q][v];
+              u[t][v] = s / rd[v][v];
             }
             if (rb + t * kOT < hi) st4(U + (size_t)(rb + t * kOT) * 4, u[t]);
           }
@@ -663,6 +668,11 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
   // V[:, J:J+B] = U R^{-1} (inside panel J/4: J % 4 + B <= 4) and its copy Q
   VT* Vp = a.V + (size_t)(J / 4) * pn;
   const int c0 = J & 3;
+  VT rf[B][B];  // the divisor factor (R2, or R1 when B = 1) in the row type
+#pragma unroll
+  for (int q = 0; q < B; ++q)
+#pragma unroll
+    for (int v = 0; v < B; ++v) rf[q][v] = (VT)(B > 1 ? Rd2[q * B + v] : Rd1[q * B + v]);
   auto final_rows = [&](int lo, int hi) {
     for (int rb = lo + threadIdx.x; rb < hi; rb += 4 * kOT) {
       VT u[4][4];
@@ -673,21 +683,22 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
       for (int t = 0; t < 4; ++t) {
         const int r = rb + t * kOT;
         if (r >= hi) continue;
-        if (B > 1) {
-#pragma unroll
-          for (int v = 0; v < B; ++v) {
-            VT s = u[t][v];
-#pragma unroll
-            for (int q = 0; q < v; ++q) s -= u[t][q] * (VT)Rd2[q * B + v];
-            u[t][v] = s / (VT)Rd2[v * B + v];
-          }
-        } else {
-          u[t][0] = u[t][0] / (VT)Rd1[0];
-        }
 #pragma unroll
         for (int v = 0; v < B; ++v) {
-          Vp[(size_t)r * 4 + c0 + v] = u[t][v];
-          a.Q[(size_t)r * 4 + v] = u[t][v];
+          VT s = u[t][v];
+#pragma unroll
+          for (int q = 0; q < v; ++q) s -= u[t][q] * rf[q][v];
+          u[t][v] = s / rf[v][v];
+        }
+        if (B == 4) {  // then J % 4 == 0: the block fills panel J / 4
+          st4(Vp + (size_t)r * 4, u[t]);
+          st4(a.Q + (size_t)r * 4, u[t]);
+        } else {
+#pragma unroll
+          for (int v = 0; v < B; ++v) {
+            Vp[(size_t)r * 4 + c0 + v] = u[t][v];
+            a.Q[(size_t)r * 4 + v] = u[t][v];
+          }
         }
       }
     }
@@ -726,7 +737,7 @@ static void orth_launch_t(const OrthPlan& p, int J, int j, cudaStream_t s) {
   a.partial = p.partial;
   a.coef = p.coef;
   a.cta_rows = p.cta_rows;
-  a.bar = GridBarrier{p.barrier, p.barrier + 1};
+  a.bar = GridBarrier{p.barrier};
   a.err = p.err;
   a.brk_step = p.brk_step;
   a.sweeps = p.sweeps;

@@ -34,7 +34,8 @@ struct StaticScratch {
   double params[kParams];
   int32_t cta_rows[kStaticMaxGrid + 1];
   uint8_t lab[kStaticMaxN];
-  unsigned words[8];  // [0] validation flags, [1] degree flags, [2..3] barrier, [4] kernel error word, [5] SpMV work
+  unsigned long long gbar;  // grid barrier arrival counter
+  unsigned words[8];        // [0] validation flags, [1] degree flags, [4] kernel error word, [5] SpMV work
 };
 
 static __device__ __align__(256) StaticScratch g_static_scratch;
@@ -93,10 +94,10 @@ static int apply_static(int64_t n64, int64_t nnz, const int32_t* row_ptr, const 
   StaticScratch* S = scratch_on(dev);
 
   // words that must start at zero: flags, barrier, error
-  check_cuda(cudaMemsetAsync(S->words, 0, sizeof(S->words), s), "clear scratch words");
+  check_cuda(cudaMemsetAsync(&S->gbar, 0, sizeof(S->gbar) + sizeof(S->words), s), "clear scratch words");
   unsigned* vflags = &S->words[0];
   unsigned* dflags = &S->words[1];
-  unsigned* barrier = &S->words[2];
+  unsigned long long* barrier = &S->gbar;
   unsigned* err = &S->words[4];
   launch_validate(n, nnz, row_ptr, col_idx, values, SFAIRSC_F32, labels, h, 0, vflags, s);
   unsigned hf[2] = {0, 0};
