@@ -232,35 +232,90 @@ __global__ void init_centroids_kernel(int d, int k, const float* __restrict__ X3
 }
 
 // ---------------------------------------------------------------- Lloyd
+// Packed pairs of float32 for the Blackwell f32x2 add / sub / mul: each half
+// is rounded on its own, exactly as the scalar operation would round it.
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void unpack2(unsigned long long v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long sub2_rn(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long mul2_rn(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+// Nearest centroid of each row.  The squared distance is the float32 sum
+// over dimensions in order of (x_j - m_j)^2, each subtract, square and add
+// rounded once; the subtracts and squares of dimensions j and j + 1 run as
+// one packed pair, and two centroids are scanned together (two independent
+// sums).  An odd dimension count is padded with x = m = 0, whose +0 term
+// leaves the sum unchanged.
 template <int DMAX>
 __global__ void assign_kernel(int n, int d, int k, const float* __restrict__ X32, const double* __restrict__ mu,
                               int* lab, float* dist, unsigned* changed, const int* __restrict__ done) {
-  extern __shared__ float msh[];  // k * d
+  static_assert(DMAX % 2 == 0, "dimension pairs");
+  extern __shared__ float msh[];  // k x dp, dp = d rounded up to even, zero padded
   const int r = blockIdx.y;
   if (done[r]) return;
-  for (int i = threadIdx.x; i < k * d; i += blockDim.x) msh[i] = __double2float_rn(mu[(size_t)r * k * d + i]);
+  const int dp = (d + 1) & ~1;
+  for (int t = threadIdx.x; t < k * dp; t += blockDim.x) {
+    const int c = t / dp, j = t - c * dp;
+    msh[t] = j < d ? __double2float_rn(mu[(size_t)r * k * d + (size_t)c * d + j]) : 0.f;
+  }
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   bool ch = false;
   if (i < n) {
     float x[DMAX];
+    if ((d & 1) == 0) {
+      const float2* xr = reinterpret_cast<const float2*>(X32 + (size_t)i * d);
 #pragma unroll
-    for (int j = 0; j < DMAX; ++j) x[j] = j < d ? X32[(size_t)i * d + j] : 0.f;
+      for (int j2 = 0; j2 < DMAX / 2; ++j2) {
+        const float2 v = 2 * j2 < d ? xr[j2] : make_float2(0.f, 0.f);
+        x[2 * j2] = v.x;
+        x[2 * j2 + 1] = v.y;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < DMAX; ++j) x[j] = j < d ? X32[(size_t)i * d + j] : 0.f;
+    }
     float best = 0.f;
     int bi = 0;
-    for (int c = 0; c < k; ++c) {
-      const float* m = msh + c * d;
-      float acc = 0.f;
+    for (int c = 0; c < k; c += 2) {
+      const int c1 = c + 1 < k ? c + 1 : c;
+      const float2* m0 = reinterpret_cast<const float2*>(msh + (size_t)c * dp);
+      const float2* m1 = reinterpret_cast<const float2*>(msh + (size_t)c1 * dp);
+      float a0 = 0.f, a1 = 0.f;
 #pragma unroll
-      for (int j = 0; j < DMAX; ++j) {
-        if (j < d) {
-          const float t = __fsub_rn(x[j], m[j]);
-          acc = __fadd_rn(acc, __fmul_rn(t, t));
+      for (int j2 = 0; j2 < DMAX / 2; ++j2) {
+        if (2 * j2 < d) {
+          const unsigned long long xp = pack2(x[2 * j2], x[2 * j2 + 1]);
+          const float2 p0 = m0[j2], p1 = m1[j2];
+          const unsigned long long t0 = sub2_rn(xp, pack2(p0.x, p0.y));
+          const unsigned long long t1 = sub2_rn(xp, pack2(p1.x, p1.y));
+          float s00, s01, s10, s11;
+          unpack2(mul2_rn(t0, t0), s00, s01);
+          unpack2(mul2_rn(t1, t1), s10, s11);
+          a0 = __fadd_rn(__fadd_rn(a0, s00), s01);
+          a1 = __fadd_rn(__fadd_rn(a1, s10), s11);
         }
       }
-      if (c == 0 || acc < best) {
-        best = acc;
+      if (c == 0 || a0 < best) {
+        best = a0;
         bi = c;
+      }
+      if (c + 1 < k && a1 < best) {
+        best = a1;
+        bi = c + 1;
       }
     }
     int* lp = lab + (size_t)r * n + i;
@@ -285,6 +340,14 @@ __global__ void update_sums_kernel(int n, int d, int k, const float* __restrict_
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const long long w0 = ((long long)blockIdx.x * nw + warp) * rows_per_warp;
   const int* lb = lab + (size_t)r * n;
+  // trunc(x 2^xshift): scaling by a power of two is exact (the scaled value
+  // stays below 2^63, and one below 2^-126 truncates to 0 either way), and the
+  // float-to-integer conversion truncates exactly
+  const bool fast = xshift >= -126 && xshift <= 127;
+  const float scale = fast ? __int_as_float((xshift + 127) << 23) : 0.f;
+  auto quant = [&](float x) -> long long {
+    return fast ? __float2ll_rz(__fmul_rn(x, scale)) : quantise_f32(x, xshift);
+  };
   int cur = -1;
   long long a0 = 0, a1 = 0, cnt = 0;
   for (long long i = w0; i < min((long long)n, w0 + rows_per_warp); ++i) {
@@ -298,8 +361,8 @@ __global__ void update_sums_kernel(int n, int d, int k, const float* __restrict_
       cur = l;
       a0 = a1 = cnt = 0;
     }
-    if (lane < d) a0 += quantise_f32(X32[(size_t)i * d + lane], xshift);
-    if (lane + 32 < d) a1 += quantise_f32(X32[(size_t)i * d + lane + 32], xshift);
+    if (lane < d) a0 += quant(X32[(size_t)i * d + lane]);
+    if (lane + 32 < d) a1 += quant(X32[(size_t)i * d + lane + 32]);
     cnt += 1;
   }
   if (cur >= 0) {
@@ -494,6 +557,7 @@ KmeansResult run_kmeans(int64_t n64, int d, const double* X, int kc, uint64_t se
       xshift = 62 - bitlen((uint64_t)n) - e;
     }
     const size_t msmem = sizeof(float) * (size_t)k * d;
+    const size_t amsmem = sizeof(float) * (size_t)k * ((d + 1) & ~1);  // padded rows for assign_kernel
     const size_t ssmem = sizeof(long long) * ((size_t)k * d + k);
     const int rows_per_warp = 64;
     const int ub = 256;
@@ -501,14 +565,14 @@ KmeansResult run_kmeans(int64_t n64, int d, const double* X, int kc, uint64_t se
     check_cuda(cudaFuncSetAttribute(update_sums_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssmem), "attr");
     auto assign = [&](void) {
       if (d <= 16) {
-        check_cuda(cudaFuncSetAttribute(assign_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem), "attr");
-        assign_kernel<16><<<dim3(nb, R), bs, msmem, s>>>(n, d, k, X32, mu, lab, dist, changed, done);
+        check_cuda(cudaFuncSetAttribute(assign_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)amsmem), "attr");
+        assign_kernel<16><<<dim3(nb, R), bs, amsmem, s>>>(n, d, k, X32, mu, lab, dist, changed, done);
       } else if (d <= 32) {
-        check_cuda(cudaFuncSetAttribute(assign_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem), "attr");
-        assign_kernel<32><<<dim3(nb, R), bs, msmem, s>>>(n, d, k, X32, mu, lab, dist, changed, done);
+        check_cuda(cudaFuncSetAttribute(assign_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)amsmem), "attr");
+        assign_kernel<32><<<dim3(nb, R), bs, amsmem, s>>>(n, d, k, X32, mu, lab, dist, changed, done);
       } else {
-        check_cuda(cudaFuncSetAttribute(assign_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem), "attr");
-        assign_kernel<64><<<dim3(nb, R), bs, msmem, s>>>(n, d, k, X32, mu, lab, dist, changed, done);
+        check_cuda(cudaFuncSetAttribute(assign_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)amsmem), "attr");
+        assign_kernel<64><<<dim3(nb, R), bs, amsmem, s>>>(n, d, k, X32, mu, lab, dist, changed, done);
       }
     };
     std::vector<int> hdone(R);
