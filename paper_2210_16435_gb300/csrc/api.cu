@@ -108,7 +108,7 @@ struct sfairsc_ctx {
   OrthPlan orth;
   double* Hh = nullptr;  // pinned host copy of the projected matrix
   double* Yh = nullptr;  // pinned host
-  float* Yfh = nullptr;  // pinned host: FP32 copy of Y for the FP32 basis
+  void* Ystage = nullptr;  // pinned host: Y row-major in the basis precision, as uploaded
 
   // results for backward / outputs
   double* X64 = nullptr;  // n x k column-major
@@ -156,7 +156,7 @@ struct sfairsc_ctx {
     for (void* p : owned) cudaFree(p);
     if (Hh) cudaFreeHost(Hh);
     if (Yh) cudaFreeHost(Yh);
-    if (Yfh) cudaFreeHost(Yfh);
+    if (Ystage) cudaFreeHost(Ystage);
     if (params_host) cudaFreeHost(params_host);
   }
 };
@@ -426,7 +426,7 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   q.sweeps = c->sweeps;
   check_cuda(cudaMallocHost((void**)&c->Hh, sizeof(double) * c->ldh * m), "pinned allocation");
   check_cuda(cudaMallocHost((void**)&c->Yh, sizeof(double) * m * m), "pinned allocation");
-  check_cuda(cudaMallocHost((void**)&c->Yfh, sizeof(float) * m * m), "pinned allocation");
+  check_cuda(cudaMallocHost(&c->Ystage, sizeof(double) * m * m), "pinned allocation");
 
   // final-stage buffers
   const int k = c->k;
@@ -523,15 +523,21 @@ struct Timer {
   }
 };
 
-// Y[:, 0:cols] (host, c->Yh) to the device in the basis precision (c->Yd holds
-// doubles, or floats in its first half for the FP32 basis).
+// Y[:, 0:cols] (host, c->Yh, column-major mv x cols) to the device, row-major
+// (row q = basis column q, cols entries) in the basis precision: c->Yd holds
+// doubles, or floats in its first half for the FP32 basis.
 void upload_y(sfairsc_ctx* c, int mv, int cols) {
   const size_t cnt = (size_t)mv * cols;
   if (c->vt == VecType::F64) {
-    check_cuda(cudaMemcpyAsync(c->Yd, c->Yh, sizeof(double) * cnt, cudaMemcpyHostToDevice, c->stream), "h2d");
+    double* st = static_cast<double*>(c->Ystage);
+    for (int q = 0; q < mv; ++q)
+      for (int i = 0; i < cols; ++i) st[(size_t)q * cols + i] = c->Yh[(size_t)i * mv + q];
+    check_cuda(cudaMemcpyAsync(c->Yd, st, sizeof(double) * cnt, cudaMemcpyHostToDevice, c->stream), "h2d");
   } else {
-    for (size_t i = 0; i < cnt; ++i) c->Yfh[i] = (float)c->Yh[i];
-    check_cuda(cudaMemcpyAsync(c->Yd, c->Yfh, sizeof(float) * cnt, cudaMemcpyHostToDevice, c->stream), "h2d");
+    float* st = static_cast<float*>(c->Ystage);
+    for (int q = 0; q < mv; ++q)
+      for (int i = 0; i < cols; ++i) st[(size_t)q * cols + i] = (float)c->Yh[(size_t)i * mv + q];
+    check_cuda(cudaMemcpyAsync(c->Yd, st, sizeof(float) * cnt, cudaMemcpyHostToDevice, c->stream), "h2d");
   }
 }
 

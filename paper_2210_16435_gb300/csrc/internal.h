@@ -112,14 +112,14 @@ struct OrthPlan {
 // as V[:, J:J+B] and its R factor in H[J:J+B, j:j+B].
 void launch_orth(const OrthPlan& p, VecType vt, int J, int j, int B, cudaStream_t s);
 int orth_max_grid(VecType vt, int B, int threads);
-// V[:, 0:K] = V[:, 0:m] Y (Y: m x K column-major FP64 on device), then V[:, K:K+B] = V[:, m:m+B].
+// V[:, 0:K] = V[:, 0:m] Y (Y: m x K row-major on device, in the basis precision), then V[:, K:K+B] = V[:, m:m+B].
 // V is stored as ldv/4 panels of n x 4 (panel p = columns 4p..4p+3).
 // Q (n x 4 row-major) receives the carried block too.
 void launch_restart(VecType vt, int n, void* V, int64_t ldv, int m, int K, int B, const void* Y, void* Q,
                     cudaStream_t s);
 // Fill V[:, 0:B] with a seeded pseudo-random block.
 void launch_random_block(VecType vt, int n, void* V, int64_t ldv, int B, uint64_t seed, cudaStream_t s);
-// X64 = V[:, 0:m] Y (Y: m x k column-major FP64), X64 n x k column-major FP64; V unchanged.
+// X64 = V[:, 0:m] Y (Y: m x k row-major, in the basis precision), X64 n x k column-major FP64; V unchanged.
 void launch_ritz(VecType vt, int n, const void* V, int64_t ldv, int m, int k, const void* Y, double* X64,
                  cudaStream_t s);
 // partial[b][c] = sum over block b's rows of (AX_c - lam_c X_c)^2.

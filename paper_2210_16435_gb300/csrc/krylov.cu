@@ -13,9 +13,12 @@ namespace sfairsc {
 // ---------------------------------------------------------------- thick restart / Ritz vectors
 // OUT[r, 0:K] = V[r, 0:m] Y[:, 0:K] for a 64-row tile: the tile of V (read
 // panel by panel, 1 KB contiguous per panel) is held transposed in shared
-// memory (stride 68), Y in 64-column chunks, and each of the 256 threads
-// accumulates a 4 x 4 block (rows 4*tr.., columns 4*tc..) from two 16-byte
-// shared loads per inner step.
+// memory (stride 68), Y (row-major, so each CTA's copy is a coalesced read) in
+// 64-column chunks, and each of the 256 threads accumulates a 4 x 4 block
+// (rows 4*tr.., columns 4*tc..) from two 16-byte shared loads per inner step.
+// The restart stores each row's 4 columns as one 16-byte write into their
+// panel; the FP64 Ritz output (column-major) goes through a shared-memory
+// tile so that each column is written as one 64-row run.
 constexpr int kTR = 64;       // rows per CTA
 constexpr int kTS = kTR + 4;  // transposed stride (keeps 16-byte alignment)
 
@@ -45,16 +48,45 @@ __global__ void __launch_bounds__(256) tile_gemm_kernel(int n, VT* V, int64_t ld
   const int rows = min(kTR, n - rbase);
   const size_t pn = (size_t)n * 4;
   const int width4 = (width + 3) & ~3;
-  for (int i = t; i < kTR * width4; i += blockDim.x) {
-    const int p = i / (kTR * 4), rem = i % (kTR * 4), rr = rem >> 2, c = 4 * p + (rem & 3);
-    if (c < width) Vt[(size_t)c * kTS + rr] = rr < rows ? V[p * pn + (size_t)(rbase + rr) * 4 + (rem & 3)] : VT(0);
+  // the tile: unit u = (panel u / kTR, row u % kTR), one row of a panel; a
+  // thread issues all its loads before its shared-memory stores
+  {
+    constexpr int UN = 8;
+    const int total = (width4 / 4) * kTR;
+    for (int u0 = t; u0 < total; u0 += 256 * UN) {
+      VT v[UN][4];
+#pragma unroll
+      for (int q = 0; q < UN; ++q) {
+        const int u = u0 + q * 256, p = u / kTR, rr = u % kTR;
+        if (u < total && rr < rows) lds4(V + p * pn + (size_t)(rbase + rr) * 4, v[q]);
+        else v[q][0] = v[q][1] = v[q][2] = v[q][3] = VT(0);
+      }
+#pragma unroll
+      for (int q = 0; q < UN; ++q) {
+        const int u = u0 + q * 256, p = u / kTR, rr = u % kTR;
+        if (u < total)
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (4 * p + e < width) Vt[(size_t)(4 * p + e) * kTS + rr] = v[q][e];
+      }
+    }
   }
   for (int k0 = 0; k0 < K; k0 += 64) {
     const int kc = min(64, K - k0);
     __syncthreads();
-    for (int i = t; i < m * 64; i += blockDim.x) {
-      const int c = i / 64, kk = i % 64;
-      Ys[i] = kk < kc ? Y[(size_t)c + (size_t)(k0 + kk) * m] : VT(0);
+    {
+      constexpr int UN = 8;
+      for (int i0 = t; i0 < m * 64; i0 += 256 * UN) {
+        VT y[UN];
+#pragma unroll
+        for (int q = 0; q < UN; ++q) {
+          const int i = i0 + q * 256, c = i >> 6, kk = i & 63;
+          y[q] = i < m * 64 && kk < kc ? Y[(size_t)c * K + k0 + kk] : VT(0);
+        }
+#pragma unroll
+        for (int q = 0; q < UN; ++q)
+          if (i0 + q * 256 < m * 64) Ys[i0 + q * 256] = y[q];
+      }
     }
     __syncthreads();
     VT acc[4][4];
@@ -71,18 +103,39 @@ __global__ void __launch_bounds__(256) tile_gemm_kernel(int n, VT* V, int64_t ld
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = fma(va[i], yb[j], acc[i][j]);
     }
+    if (MODE == 0) {
+      // columns k0 + 4 tc .. + 3 form panel (k0 + 4 tc) / 4 (k0 is a multiple of 64)
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int rr = 4 * tr + i;
-      if (rr >= rows) continue;
-      const int r = rbase + rr;
+      for (int i = 0; i < 4; ++i) {
+        const int rr = 4 * tr + i;
+        if (rr >= rows) continue;
+        const int r = rbase + rr;
+        VT* dst = V + ((k0 + 4 * tc) >> 2) * pn + (size_t)r * 4;
+        if (4 * tc + 4 <= kc) {
+          if constexpr (sizeof(VT) == 4) {
+            *reinterpret_cast<float4*>(dst) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+          } else {
+            reinterpret_cast<double2*>(dst)[0] = make_double2(acc[i][0], acc[i][1]);
+            reinterpret_cast<double2*>(dst)[1] = make_double2(acc[i][2], acc[i][3]);
+          }
+        } else {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int col = 4 * tc + j;
-        if (col < kc) {
-          if (MODE == 0) V[((k0 + col) >> 2) * pn + (size_t)r * 4 + ((k0 + col) & 3)] = acc[i][j];
-          else X[(size_t)r + (size_t)(k0 + col) * n] = (double)acc[i][j];
+          for (int j = 0; j < 4; ++j)
+            if (4 * tc + j < kc) dst[j] = acc[i][j];
         }
+      }
+    } else {
+      // through shared memory (the Y chunk's space, after every thread is done with it)
+      double* Xs = reinterpret_cast<double*>(Ys);  // 64 columns x (kTR + 1)
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) Xs[(size_t)(4 * tc + j) * (kTR + 1) + 4 * tr + i] = (double)acc[i][j];
+      __syncthreads();
+      for (int e = t; e < kc * kTR; e += blockDim.x) {
+        const int col = e / kTR, rr = e % kTR;
+        if (rr < rows) X[(size_t)(rbase + rr) + (size_t)(k0 + col) * n] = Xs[(size_t)col * (kTR + 1) + rr];
       }
     }
   }
@@ -100,7 +153,9 @@ __global__ void __launch_bounds__(256) tile_gemm_kernel(int n, VT* V, int64_t ld
 template <typename VT, int MODE>
 static void tile_gemm_launch(int n, VT* V, int64_t ldv, int m, int K, int B, const VT* Y, VT* Q, double* X,
                              cudaStream_t s) {
-  const size_t smem = sizeof(VT) * ((size_t)(m + B) * kTS + (size_t)m * 64);
+  size_t smem = sizeof(VT) * ((size_t)(m + B) * kTS + (size_t)m * 64);
+  if (MODE == 1)  // the Y chunk's space also holds the 64 x (kTR + 1) FP64 output tile
+    smem = std::max(smem, sizeof(VT) * (size_t)(m + B) * kTS + sizeof(double) * 64 * (kTR + 1));
   if (smem > 227 * 1024) fail(SFAIRSC_ERR_UNSUPPORTED, "Krylov basis too wide for the restart tile in this precision");
   auto kern = tile_gemm_kernel<VT, MODE>;
   check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "tile gemm smem");

@@ -318,6 +318,7 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
     constexpr int CH = (int)sizeof(VT) / 4;
     const SliceShape sh = slice_shape<VT>(np);
     const int SR = sh.sr, LPA = sh.lpa, rsc = sh.rsc;
+    const int lsr = 31 - __clz(SR);  // SR is a power of two
     const int sbytes = SR * rsc * 16;  // one slice
     const int LPR = NC == 1 ? lanes_for(np) : 32;
     const int RPW = 32 / LPR;
@@ -330,13 +331,15 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
       if (sl < nsl) {
         const int rb = r0 + sl * SR;
         unsigned char* dst = wbuf + (k & 1) * sbytes;
-        for (int idx = lane; idx < SR * ncols; idx += 32) {
-          const int i = idx % SR, c = idx / SR;  // lanes run down a column: coalesced rows
-          const int col = c / CH, part = c % CH;
-          const bool valid = rb + i < r1;
-          const int row = valid ? rb + i : r0;
-          const VT* src = (col < np ? a.V + col * pn : U) + (size_t)row * 4 + part * (4 / CH);
-          cp_async16(dst + ((size_t)i * rsc + c) * 16, src, valid);
+        // lane: row i, chunks c0, c0 + 32 / SR, ... (lanes run down a column: coalesced rows)
+        const int i = lane & (SR - 1);
+        const bool valid = rb + i < r1;
+        const size_t roff = (size_t)(valid ? rb + i : r0) * 4;
+        unsigned char* d = dst + (size_t)i * rsc * 16;
+        for (int c = lane >> lsr; c < ncols; c += 32 >> lsr) {
+          const int col = CH == 1 ? c : c >> 1;
+          const VT* base = col < np ? a.V + (size_t)col * pn : U;
+          cp_async16(d + c * 16, base + roff + (CH == 1 ? 0 : (c & 1) * 2), valid);
         }
       }
       cp_async_commit();
