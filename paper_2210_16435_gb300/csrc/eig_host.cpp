@@ -1,26 +1,42 @@
 // Dense symmetric eigensolver for the small projected matrix of the Krylov
 // method (size m <= 256, FP64): Householder reduction to tridiagonal form,
-// then implicit symmetric QR steps with the Wilkinson shift, accumulating
-// the orthogonal transforms (Golub and Van Loan, Matrix Computations,
-// Sec. 8.3).  Eigenvalues are returned ascending with their vectors.
+// then implicit symmetric QR steps with the Wilkinson shift (Golub and Van
+// Loan, Matrix Computations, Sec. 8.3).  Eigenvalues are returned ascending
+// with their vectors.
+//
+// Neither the reduction's reflectors nor the QR rotations depend on the
+// eigenvector matrix, so both are recorded and the vectors are formed
+// afterwards row by row: row r of Q is e_r^T H_0 H_1 ... G_1 G_2 ..., the
+// same operations on each row as accumulating Q transform by transform.
+// Rows are independent, so blocks of rows go to a few host threads.
 #include <algorithm>
 #include <cmath>
 #include <numeric>
+#include <thread>
 #include <vector>
 
 #include "internal.h"
 
 namespace sfairsc {
 
+namespace {
+
+struct Rotation {
+  int k;
+  double c, s;  // (x_k, x_k+1) <- (c x_k - s x_k+1, s x_k + c x_k+1)
+};
+
+}  // namespace
+
 void host_symmetric_eig(int m, double* A, double* w) {
   // A: m x m column-major symmetric; on exit its columns are the eigenvectors.
-  std::vector<double> Q((size_t)m * m, 0.0);
-  for (int i = 0; i < m; ++i) Q[(size_t)i * m + i] = 1.0;
   auto a = [&](int i, int j) -> double& { return A[(size_t)j * m + i]; };
-  auto q = [&](int i, int j) -> double& { return Q[(size_t)j * m + i]; };
 
-  // Householder: for column k, reflect x = A[k+1:, k] onto alpha e_1.
-  std::vector<double> v(m), p(m), wv(m);
+  // Householder: for column k, reflect x = A[k+1:, k] onto alpha e_1.  The
+  // reflector I - beta v v^T (v over rows k+1..m-1) is kept for the vectors.
+  std::vector<double> refl((size_t)m * m, 0.0);  // v of step k at refl[k * m + k + 1 ..]
+  std::vector<double> rbeta(m, 0.0);             // 0: no reflection at this step
+  std::vector<double> p(m), wv(m);
   for (int k = 0; k + 2 < m; ++k) {
     const int len = m - k - 1;
     double sig = 0.0;
@@ -29,18 +45,22 @@ void host_symmetric_eig(int m, double* A, double* w) {
     if (sig == 0.0) continue;
     const double x0 = a(k + 1, k);
     const double alpha = x0 >= 0.0 ? -sig : sig;
+    double* v = &refl[(size_t)k * m + k + 1];
     for (int i = 0; i < len; ++i) v[i] = a(k + 1 + i, k);
     v[0] -= alpha;
     double vv = 0.0;
     for (int i = 0; i < len; ++i) vv += v[i] * v[i];
     if (vv == 0.0) continue;
     const double beta = 2.0 / vv;
-    // p = beta * A22 v
-    for (int i = 0; i < len; ++i) {
-      double s = 0.0;
-      for (int j = 0; j < len; ++j) s += a(k + 1 + i, k + 1 + j) * v[j];
-      p[i] = beta * s;
+    rbeta[k] = beta;
+    // p = beta * A22 v, down the columns of A22
+    for (int i = 0; i < len; ++i) p[i] = 0.0;
+    for (int j = 0; j < len; ++j) {
+      const double vj = v[j];
+      const double* col = &A[(size_t)(k + 1 + j) * m + k + 1];
+      for (int i = 0; i < len; ++i) p[i] += col[i] * vj;
     }
+    for (int i = 0; i < len; ++i) p[i] *= beta;
     double vp = 0.0;
     for (int i = 0; i < len; ++i) vp += v[i] * p[i];
     const double K = 0.5 * beta * vp;
@@ -53,13 +73,6 @@ void host_symmetric_eig(int m, double* A, double* w) {
       a(k + 1 + i, k) = 0.0;
       a(k, k + 1 + i) = 0.0;
     }
-    // Q <- Q (I - beta v v^T) on columns k+1..m-1
-    for (int r = 0; r < m; ++r) {
-      double s = 0.0;
-      for (int j = 0; j < len; ++j) s += q(r, k + 1 + j) * v[j];
-      s *= beta;
-      for (int j = 0; j < len; ++j) q(r, k + 1 + j) -= s * v[j];
-    }
   }
   std::vector<double> d(m), e(std::max(m - 1, 1), 0.0);
   for (int i = 0; i < m; ++i) d[i] = a(i, i);
@@ -67,6 +80,8 @@ void host_symmetric_eig(int m, double* A, double* w) {
 
   // Implicit symmetric QR with Wilkinson shift on the unreduced trailing block.
   const double eps = std::numeric_limits<double>::epsilon();
+  std::vector<Rotation> rot;
+  rot.reserve((size_t)8 * m * m);
   int hi = m - 1;
   int guard = 0;
   while (hi > 0 && guard < 60 * m) {
@@ -84,12 +99,15 @@ void host_symmetric_eig(int m, double* A, double* w) {
     const double mu = d[hi] - (den != 0.0 ? bb * bb / den : 0.0);
     double x = d[lo] - mu, z = e[lo];
     for (int k = lo; k < hi; ++k) {
-      const double r = std::hypot(x, z);
+      // entries of the projected matrix are far from the overflow range, so
+      // the plain root serves (std::hypot's scaling dominated the loop)
+      const double r = std::sqrt(x * x + z * z);
       double c = 1.0, s = 0.0;
       if (r != 0.0) {
         c = x / r;
         s = -z / r;
       }
+      rot.push_back(Rotation{k, c, s});
       if (k > lo) e[k - 1] = c * e[k - 1] - s * z;
       const double ak = d[k], ak1 = d[k + 1], bk = e[k];
       d[k] = c * c * ak - 2.0 * c * s * bk + s * s * ak1;
@@ -100,19 +118,78 @@ void host_symmetric_eig(int m, double* A, double* w) {
         e[k + 1] = c * e[k + 1];
         x = e[k];
       }
-      for (int rr = 0; rr < m; ++rr) {
-        const double qk = q(rr, k), qk1 = q(rr, k + 1);
-        q(rr, k) = c * qk - s * qk1;
-        q(rr, k + 1) = s * qk + c * qk1;
-      }
     }
   }
   std::vector<int> order(m);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int i, int j) { return d[i] < d[j]; });
+  std::vector<int> where(m);  // column of Q that lands in output column c
   for (int c = 0; c < m; ++c) {
     w[c] = d[order[c]];
-    for (int r = 0; r < m; ++r) A[(size_t)c * m + r] = Q[(size_t)order[c] * m + r];
+    where[c] = order[c];
+  }
+
+  // Rows [r0, r1) of Q = I H_0 H_1 ... (rotations in order), written to A's
+  // columns in ascending eigenvalue order.  A is free: d and e hold T.  Eight
+  // rows at a time, held column by column (x[j * 8 + t] = row t's entry j),
+  // so every reflector and rotation acts on contiguous 8-row vectors.
+  auto rows = [&](int r0, int r1) {
+    constexpr int W = 8;
+    std::vector<double> x((size_t)m * W);
+    for (int b0 = r0; b0 < r1; b0 += W) {
+      const int nr = std::min(W, r1 - b0);
+      std::fill(x.begin(), x.end(), 0.0);
+      for (int t = 0; t < nr; ++t) x[(size_t)(b0 + t) * W + t] = 1.0;
+      for (int k = 0; k + 2 < m; ++k) {
+        const double beta = rbeta[k];
+        if (beta == 0.0) continue;
+        const double* v = &refl[(size_t)k * m + k + 1];
+        const int len = m - k - 1;
+        double s[W] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int j = 0; j < len; ++j) {
+          const double* xj = &x[(size_t)(k + 1 + j) * W];
+          for (int t = 0; t < W; ++t) s[t] += xj[t] * v[j];
+        }
+        for (int t = 0; t < W; ++t) s[t] *= beta;
+        for (int j = 0; j < len; ++j) {
+          double* xj = &x[(size_t)(k + 1 + j) * W];
+          for (int t = 0; t < W; ++t) xj[t] -= s[t] * v[j];
+        }
+      }
+      for (const Rotation& g : rot) {
+        double* x0 = &x[(size_t)g.k * W];
+        double* x1 = x0 + W;
+        for (int t = 0; t < W; ++t) {
+          const double a0 = x0[t], a1 = x1[t];
+          x0[t] = g.c * a0 - g.s * a1;
+          x1[t] = g.s * a0 + g.c * a1;
+        }
+      }
+      for (int c = 0; c < m; ++c)
+        for (int t = 0; t < nr; ++t) A[(size_t)c * m + b0 + t] = x[(size_t)where[c] * W + t];
+    }
+  };
+  // whole 8-row blocks per thread
+  const int nb = (m + 7) / 8;
+  const unsigned hw = std::thread::hardware_concurrency();
+  const int nt = m < 48 ? 1 : (int)std::min<unsigned>({8u, std::max(1u, hw / 2), (unsigned)nb});
+  if (nt <= 1) {
+    rows(0, m);
+  } else {
+    auto range = [&](int t, int& lo, int& hi2) {
+      lo = std::min(m, (t * nb / nt) * 8);
+      hi2 = std::min(m, ((t + 1) * nb / nt) * 8);
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nt; ++t) {
+      int lo, hi2;
+      range(t, lo, hi2);
+      pool.emplace_back(rows, lo, hi2);
+    }
+    int lo, hi2;
+    range(0, lo, hi2);
+    rows(lo, hi2);
+    for (auto& th : pool) th.join();
   }
 }
 
