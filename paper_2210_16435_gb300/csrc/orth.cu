@@ -62,6 +62,11 @@ struct Acc<float> {
     k.reduce(from);
   }
   __device__ __forceinline__ double value() const { return k.value(); }
+  // the (sum, carry) pair packed into 8 bytes, to be combined by slot_sum
+  // without FP64 arithmetic in every lane (after reduce)
+  __device__ __forceinline__ double slot() const {
+    return __longlong_as_double((long long)(((unsigned long long)__float_as_uint(k.c) << 32) | __float_as_uint(k.s)));
+  }
 };
 template <>
 struct Acc<double> {
@@ -73,7 +78,29 @@ struct Acc<double> {
     for (int o = from; o < 32; o <<= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
   }
   __device__ __forceinline__ double value() const { return w; }
+  __device__ __forceinline__ double slot() const { return w; }
 };
+
+// Sum of n slots p[0], p[stride], ... written by Acc::slot(): FP32 (sum,
+// carry) pairs are added by TwoSum and converted to FP64 once; FP64 slots
+// are added in FP64.  Fixed order.
+template <typename VT>
+__device__ __forceinline__ double slot_sum(const double* p, int n, int stride) {
+  if constexpr (sizeof(VT) == 4) {
+    Comp32 t;
+    t.zero();
+    for (int i = 0; i < n; ++i) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(p[(size_t)i * stride]);
+      t.add(__uint_as_float((unsigned)b));
+      t.add(__uint_as_float((unsigned)(b >> 32)));
+    }
+    return t.value();
+  } else {
+    double t = 0.0;
+    for (int i = 0; i < n; ++i) t += p[(size_t)i * stride];
+    return t;
+  }
+}
 
 template <typename VT>
 __device__ __forceinline__ void ld4(const VT* p, VT (&x)[4]) {
@@ -479,19 +506,19 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
           for (int jj = 0; jj < 4; ++jj)
             if (4 * pp + jj < J)
 #pragma unroll
-              for (int v = 0; v < B; ++v) rw[(4 * pp + jj) * B + v] = acc[q][jj][v].value();
+              for (int v = 0; v < B; ++v) rw[(4 * pp + jj) * B + v] = acc[q][jj][v].slot();
       }
     if (lane == 0) {
       if (kind == 0) {
 #pragma unroll
-        for (int v = 0; v < B; ++v) rw[kXo + v] = ga[v].value();
+        for (int v = 0; v < B; ++v) rw[kXo + v] = ga[v].slot();
       } else {
         int e = 0;
 #pragma unroll
         for (int v = 0; v < B; ++v)
 #pragma unroll
           for (int w2 = v; w2 < B; ++w2) {
-            const double g = ga[e++].value();
+            const double g = ga[e++].slot();
             rw[kXo + v * B + w2] = g;
             rw[kXo + w2 * B + v] = g;
           }
@@ -499,17 +526,12 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
     }
     __syncthreads();
     if (want_c)
-      for (int i = threadIdx.x; i < P; i += blockDim.x) {
-        double s = 0.0;
-        for (int w = 0; w < kOW; ++w) s += red[(size_t)w * kRed + i];
-        a.partial[(size_t)blockIdx.x * kStride + i] = s;
-      }
+      for (int i = threadIdx.x; i < P; i += blockDim.x)
+        a.partial[(size_t)blockIdx.x * kStride + i] = slot_sum<VT>(red + i, kOW, kRed);
     const int ne = kind == 0 ? B : B * B;
-    if ((int)threadIdx.x < ne) {
-      double s = 0.0;
-      for (int w = 0; w < kOW; ++w) s += red[(size_t)w * kRed + kXo + threadIdx.x];
-      a.partial[(size_t)blockIdx.x * kStride + (kind == 0 ? kNormOff : kGramOff) + threadIdx.x] = s;
-    }
+    if ((int)threadIdx.x < ne)
+      a.partial[(size_t)blockIdx.x * kStride + (kind == 0 ? kNormOff : kGramOff) + threadIdx.x] =
+          slot_sum<VT>(red + kXo + threadIdx.x, kOW, kRed);
     return true;
   };
 
@@ -568,17 +590,14 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
       for (int v = 0; v < B; ++v)
 #pragma unroll
         for (int w2 = v; w2 < B; ++w2) {
-          const double x = g[e++].value();
+          const double x = g[e++].slot();
           scratch[warp * 16 + v * B + w2] = x;
           scratch[warp * 16 + w2 * B + v] = x;
         }
     }
     __syncthreads();
-    if ((int)threadIdx.x < B * B) {
-      double s = 0.0;
-      for (int w = 0; w < kOW; ++w) s += scratch[w * 16 + threadIdx.x];
-      a.partial[(size_t)blockIdx.x * kStride + off + threadIdx.x] = s;
-    }
+    if ((int)threadIdx.x < B * B)
+      a.partial[(size_t)blockIdx.x * kStride + off + threadIdx.x] = slot_sum<VT>(scratch + threadIdx.x, kOW, 16);
   };
 
   // Cholesky of gram_s = R^T R (R upper).  A column whose remaining norm
