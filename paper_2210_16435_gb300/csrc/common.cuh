@@ -119,7 +119,25 @@ struct Comp32 {
     }
   }
   __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+  // (s, c) packed into 8 bytes, for comp32_slot_sum: lets many pairs be
+  // combined in FP32 with one conversion to FP64 at the end
+  __device__ __forceinline__ double slot() const {
+    return __longlong_as_double((long long)(((unsigned long long)__float_as_uint(c) << 32) | __float_as_uint(s)));
+  }
 };
+
+// Sum of n packed pairs p[0], p[stride], ... (Comp32::slot) by TwoSum in
+// FP32, in order, converted to FP64 once.
+__device__ __forceinline__ double comp32_slot_sum(const double* p, int n, int stride) {
+  Comp32 t;
+  t.zero();
+  for (int i = 0; i < n; ++i) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(p[(size_t)i * stride]);
+    t.add(__uint_as_float((unsigned)b));
+    t.add(__uint_as_float((unsigned)(b >> 32)));
+  }
+  return t.value();
+}
 
 // Nanosecond global timer (PTX %globaltimer).
 __device__ __forceinline__ unsigned long long globaltimer_ns() {

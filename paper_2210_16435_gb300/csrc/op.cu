@@ -163,8 +163,9 @@ __device__ __forceinline__ void solve_groups(const double* tot, const double* pa
 // partial[blockIdx.x][s * B + v] = sum over own rows i in V_s of f(i)_v.
 // Thread per row; groups are taken 4 per pass with predicated adds (no
 // per-row shuffles).  FP32: per-thread windows of 16 rows carried by TwoSum,
-// combined over the warp by a TwoSum tree; FP64: FP64 throughout.  Warps are
-// then added in a fixed order, so the result is bitwise reproducible.
+// combined over the warp by a TwoSum tree and over warps by TwoSum, then
+// converted to FP64 once; FP64: FP64 throughout.  Warps are added in a fixed
+// order, so the result is bitwise reproducible.
 template <typename VT, int B, typename F>
 __device__ void cta_group_sums(int r0, int r1, int h, const uint8_t* __restrict__ lab, double* red, double* partial,
                                F&& f) {
@@ -223,7 +224,7 @@ __device__ void cta_group_sums(int r0, int r1, int h, const uint8_t* __restrict_
       if (lane == 0)
         for (int j = 0; j < 4 && s0 + j < h; ++j)
 #pragma unroll
-          for (int v = 0; v < B; ++v) red[warp * P + (s0 + j) * B + v] = acc[j][v].value();
+          for (int v = 0; v < B; ++v) red[warp * P + (s0 + j) * B + v] = acc[j][v].slot();
     } else {
       double acc[4][B];
 #pragma unroll
@@ -253,9 +254,15 @@ __device__ void cta_group_sums(int r0, int r1, int h, const uint8_t* __restrict_
     }
   }
   __syncthreads();
+  // warps in a fixed order: FP32 (sum, carry) pairs by TwoSum, one conversion
+  // per value (no FP64 arithmetic per warp); FP64 values in FP64
   for (int p = threadIdx.x; p < P; p += blockDim.x) {
     double s = 0.0;
-    for (int wv = 0; wv < nwarps; ++wv) s += red[wv * P + p];
+    if constexpr (sizeof(VT) == 4) {
+      s = comp32_slot_sum(red + p, nwarps, P);
+    } else {
+      for (int wv = 0; wv < nwarps; ++wv) s += red[wv * P + p];
+    }
     partial[(size_t)blockIdx.x * P + p] = s;
   }
   __syncthreads();

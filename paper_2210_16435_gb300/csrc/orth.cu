@@ -64,9 +64,7 @@ struct Acc<float> {
   __device__ __forceinline__ double value() const { return k.value(); }
   // the (sum, carry) pair packed into 8 bytes, to be combined by slot_sum
   // without FP64 arithmetic in every lane (after reduce)
-  __device__ __forceinline__ double slot() const {
-    return __longlong_as_double((long long)(((unsigned long long)__float_as_uint(k.c) << 32) | __float_as_uint(k.s)));
-  }
+  __device__ __forceinline__ double slot() const { return k.slot(); }
 };
 template <>
 struct Acc<double> {
@@ -87,14 +85,7 @@ struct Acc<double> {
 template <typename VT>
 __device__ __forceinline__ double slot_sum(const double* p, int n, int stride) {
   if constexpr (sizeof(VT) == 4) {
-    Comp32 t;
-    t.zero();
-    for (int i = 0; i < n; ++i) {
-      const unsigned long long b = (unsigned long long)__double_as_longlong(p[(size_t)i * stride]);
-      t.add(__uint_as_float((unsigned)b));
-      t.add(__uint_as_float((unsigned)(b >> 32)));
-    }
-    return t.value();
+    return comp32_slot_sum(p, n, stride);
   } else {
     double t = 0.0;
     for (int i = 0; i < n; ++i) t += p[(size_t)i * stride];
