@@ -212,6 +212,14 @@ __device__ void warps_to_loc(Sm& S, int slot, int cnt) {
   __syncthreads();
 }
 
+// The same for red entries holding packed FP32 (sum, carry) pairs (Comp::slot):
+// the warps' pairs are added by TwoSum in FP32 and converted to FP64 once.
+__device__ void warps_to_loc_pairs(Sm& S, int slot, int cnt) {
+  __syncthreads();
+  for (int i = threadIdx.x; i < cnt; i += kT) S.loc[i] = comp32_slot_sum(S.red + i, kW, slot);
+  __syncthreads();
+}
+
 __device__ void zero_red(Sm& S, int slot, int cnt) {
   __syncthreads();
   for (int i = threadIdx.x; i < kW * slot; i += kT)
@@ -308,6 +316,10 @@ struct Comp {
     c = __fadd_rn(c, e);
   }
   __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+  // the pair packed into 8 bytes (see warps_to_loc_pairs)
+  __device__ __forceinline__ double slot() const {
+    return __longlong_as_double((long long)(((unsigned long long)__float_as_uint(c) << 32) | __float_as_uint(s)));
+  }
 };
 
 // Sum over the lanes whose ids differ only in bits >= `from` (xor tree, TwoSum
@@ -372,7 +384,7 @@ __device__ void group_sums_f32(Sm& S, int slot, int r0, int r1, int h, const uin
     if (lane == 0)
       for (int j = 0; j < 4 && s0 + j < h; ++j)
 #pragma unroll
-        for (int v = 0; v < kB; ++v) S.red[warp * slot + (s0 + j) * kB + v] = acc[j][v].value();
+        for (int v = 0; v < kB; ++v) S.red[warp * slot + (s0 + j) * kB + v] = acc[j][v].slot();
   }
 }
 
@@ -716,8 +728,8 @@ __device__ void gram_pass(const Job& J, Sm& S, Team& T, const Layout& L, int r0,
   }
   __syncthreads();
   if (lane == 0)
-    for (int e = 0; e < 10; ++e) S.red[warp * L.slot + e] = ga[e].value();
-  warps_to_loc(S, L.slot, 10);
+    for (int e = 0; e < 10; ++e) S.red[warp * L.slot + e] = ga[e].slot();
+  warps_to_loc_pairs(S, L.slot, 10);
   team_reduce(T, S, 10);
   gram_unpack(S, S.tot);
 }
@@ -880,11 +892,11 @@ __device__ bool orth_block(const Job& J, Sm& S, Team& T, const Layout& L, long& 
 #pragma unroll
         for (int j = 0; j < 4; ++j)
 #pragma unroll
-          for (int v = 0; v < kB; ++v) S.red[warp * slot + (4 * p + j) * kB + v] = acc[j][v].value();
+          for (int v = 0; v < kB; ++v) S.red[warp * slot + (4 * p + j) * kB + v] = acc[j][v].slot();
       if (lane == 0)
 #pragma unroll
-        for (int e = 0; e < 10; ++e) S.red[warp * slot + x0 + e] = ga[e].value();
-      warps_to_loc(S, slot, x0 + 10);
+        for (int e = 0; e < 10; ++e) S.red[warp * slot + x0 + e] = ga[e].slot();
+      warps_to_loc_pairs(S, slot, x0 + 10);
       team_reduce(T, S, x0 + 10);
       ++sweeps;
     };
@@ -929,7 +941,7 @@ __device__ bool orth_block(const Job& J, Sm& S, Team& T, const Layout& L, long& 
 #pragma unroll
     for (int v = 0; v < kB; ++v) x[v] = d * u[v];
   });
-  warps_to_loc(S, slot, h * kB);
+  warps_to_loc_pairs(S, slot, h * kB);
   team_reduce(T, S, h * kB);
   if (h > 1) {
     solve_groups(S, S.tot, h, S.av, S.coefA, S.coefAf);
@@ -969,7 +981,7 @@ __device__ void operator_f32(const Job& J, Sm& S, Team& T, const Layout& L, int 
       x[2] = d * t.z;
       x[3] = d * t.w;
     });
-    warps_to_loc(S, L.slot, J.h * kB);
+    warps_to_loc_pairs(S, L.slot, J.h * kB);
     team_reduce(T, S, J.h * kB);
     solve_groups(S, S.tot, J.h, S.coefD, S.cs);                   // b into coefD
     deflate_coef(S, J.h, sigma, S.coefD, S.av, S.coefD, S.coefDf);  // same thread reads b before writing
@@ -1679,7 +1691,7 @@ __device__ void solve_graph(const Job& J, Stat* st, const Params& prm, Sm& S, Te
         x[2] = d * t.z;
         x[3] = d * t.w;
       });
-      warps_to_loc(S, slot, h * kB);
+      warps_to_loc_pairs(S, slot, h * kB);
       team_reduce(T, S, h * kB);
       if (h > 1) {
         solve_groups(S, S.tot, h, S.av, S.coefA, S.coefAf);
