@@ -34,7 +34,7 @@ def eiglib():
     return lib
 
 
-@pytest.mark.parametrize("m,seed", [(1, 0), (2, 1), (5, 2), (20, 3), (64, 4), (136, 5)])
+@pytest.mark.parametrize("m,seed", [(1, 0), (2, 1), (5, 2), (20, 3), (64, 4), (100, 6), (136, 5), (250, 7)])
 def test_random_symmetric(eiglib, m, seed):
     rng = np.random.default_rng(seed)
     A = rng.standard_normal((m, m))
