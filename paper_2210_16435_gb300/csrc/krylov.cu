@@ -74,7 +74,25 @@ __global__ void __launch_bounds__(256) tile_gemm_kernel(int n, VT* V, int64_t ld
   for (int k0 = 0; k0 < K; k0 += 64) {
     const int kc = min(64, K - k0);
     __syncthreads();
-    {
+    if (sizeof(VT) == 4 && (K & 3) == 0) {
+      // 16-byte pieces (c, 4 kk4): the whole chunk in one round of loads
+      constexpr int UN = 8;
+      const int nq = m * 16;
+      for (int i0 = t; i0 < nq; i0 += 256 * UN) {
+        float4 y[UN];
+#pragma unroll
+        for (int q = 0; q < UN; ++q) {
+          const int i = i0 + q * 256, c = i >> 4, kk = (i & 15) * 4;
+          y[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (i < nq && kk < kc) y[q] = *reinterpret_cast<const float4*>(Y + (size_t)c * K + k0 + kk);  // kc % 4 == 0
+        }
+#pragma unroll
+        for (int q = 0; q < UN; ++q) {
+          const int i = i0 + q * 256;
+          if (i < nq) *reinterpret_cast<float4*>(Ys + (size_t)(i >> 4) * 64 + (i & 15) * 4) = y[q];
+        }
+      }
+    } else {
       constexpr int UN = 8;
       for (int i0 = t; i0 < m * 64; i0 += 256 * UN) {
         VT y[UN];

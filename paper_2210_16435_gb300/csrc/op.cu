@@ -184,12 +184,13 @@ __device__ void cta_group_sums(int r0, int r1, int h, const uint8_t* __restrict_
         }
       int cnt = 0;
       const int T = blockDim.x;
-      for (int r = r0 + threadIdx.x; r < r1; r += 4 * T) {
-        // four rows' loads in flight before their adds
-        int g[4];
-        float x[4][B];
+      constexpr int RF = B == 4 ? 2 : 4;  // rows in flight (fewer at B = 4: registers)
+      for (int r = r0 + threadIdx.x; r < r1; r += RF * T) {
+        // RF rows' loads in flight before their adds
+        int g[RF];
+        float x[RF][B];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {  // loads are not predicated on the label (one round trip)
+        for (int k = 0; k < RF; ++k) {  // loads are not predicated on the label (one round trip)
           const int rk = r + k * T;
           g[k] = rk < r1 ? (int)lab[rk] - s0 : -1;
           if (rk < r1) f(rk, x[k]);
@@ -198,12 +199,12 @@ __device__ void cta_group_sums(int r0, int r1, int h, const uint8_t* __restrict_
             for (int v = 0; v < B; ++v) x[k][v] = 0.f;
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < RF; ++k)
 #pragma unroll
           for (int j = 0; j < 4; ++j)
 #pragma unroll
             for (int v = 0; v < B; ++v) win[j][v] += g[k] == j ? x[k][v] : 0.f;
-        if (++cnt == 4) {
+        if (++cnt == 16 / RF) {  // windows of 16 rows
 #pragma unroll
           for (int j = 0; j < 4; ++j)
 #pragma unroll
