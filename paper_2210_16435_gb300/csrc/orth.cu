@@ -389,7 +389,23 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
         for (int v = 0; v < B; ++v) d[v] = VT(0);
         if (upd) {
           const int nfull = J >> 2;  // panels whose 4 columns are all < J
-          for (int pp = g; pp < nfull; pp += LPA) {
+          VT d1[B];  // a second set of chains: two panels' loads in flight per step
+#pragma unroll
+          for (int v = 0; v < B; ++v) d1[v] = VT(0);
+          int pp = g;
+          for (; pp + LPA < nfull; pp += 2 * LPA) {
+            VT x0[4], x1[4];
+            ld4(at(i, pp), x0);
+            ld4(at(i, pp + LPA), x1);
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+              for (int v = 0; v < B; ++v) {
+                d[v] = fma(x0[jj], cfs[(4 * pp + jj) * B + v], d[v]);
+                d1[v] = fma(x1[jj], cfs[(4 * (pp + LPA) + jj) * B + v], d1[v]);
+              }
+          }
+          if (pp < nfull) {
             VT x[4];
             ld4(at(i, pp), x);
 #pragma unroll
@@ -402,8 +418,10 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
             ld4(at(i, nfull), x);
             for (int jj = 0; jj < (J & 3); ++jj)
 #pragma unroll
-              for (int v = 0; v < B; ++v) d[v] = fma(x[jj], cfs[(4 * nfull + jj) * B + v], d[v]);
+              for (int v = 0; v < B; ++v) d1[v] = fma(x[jj], cfs[(4 * nfull + jj) * B + v], d1[v]);
           }
+#pragma unroll
+          for (int v = 0; v < B; ++v) d[v] += d1[v];
           for (int o = 1; o < LPA; o <<= 1)
 #pragma unroll
             for (int v = 0; v < B; ++v) d[v] += __shfl_xor_sync(0xffffffffu, d[v], o);
