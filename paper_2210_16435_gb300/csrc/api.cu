@@ -590,7 +590,6 @@ double final_check(sfairsc_ctx* c, int mv, const std::vector<double>& T, std::ve
 int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* labels, sfairsc_info* info) {
   cudaStream_t s = c->stream;
   const int n = (int)c->n, k = c->k, B = c->B, m = c->m, ldh = c->ldh;
-  const size_t vs = c->vt == VecType::F64 ? 8 : 4;
   const int kNoBreak = std::numeric_limits<int>::max();
   sfairsc_info inf{};
   inf.sigma = c->sigma;

@@ -272,7 +272,7 @@ __device__ void cta_group_sums(int r0, int r1, int h, const uint8_t* __restrict_
 template <typename VT, typename MT, int B>
 __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   const int h = a.h;
   const int P = h * B;
   const bool grouped = h > 1;
