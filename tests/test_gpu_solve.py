@@ -27,11 +27,11 @@ def eig_rel_err(got, ref, sigma, tol):
     return rel.max()
 
 
-def solve_and_check(g, k, prec, block=1, lam_tol=None, normalized=True, ref=None, vdt=torch.float64):
+def solve_and_check(g, k, prec, block=1, lam_tol=None, normalized=True, ref=None, vdt=torch.float64, basis=0):
     from paper_2210_16435_gb300.solver import FairSC
 
     rp, ci, v, gr = graph_tensors(g, vdt)
-    s = FairSC(rp, ci, v, gr, k=k, h=g.h, prec=prec, block=block, normalized=normalized)
+    s = FairSC(rp, ci, v, gr, k=k, h=g.h, prec=prec, block=block, normalized=normalized, basis=basis)
     lam, H, lab, info = s.solve()
     lam, H, lab = lam.cpu().numpy(), H.cpu().numpy(), lab.cpu().numpy()
     W = sp.csr_matrix((v.double().cpu().numpy(), g.col_idx, g.row_ptr), shape=(g.n, g.n))
@@ -96,6 +96,15 @@ def test_block_lanczos(built_lib, block):
     g = configs.msbm_n2000_k5_h2()["graph"]
     solve_and_check(g, 5, "fp64", block=block)
     solve_and_check(g, 5, "mixed", block=block)
+
+
+@pytest.mark.parametrize("prec,block", [("mixed", 4), ("fp64", 1)])
+def test_wide_basis(built_lib, prec, block):
+    """A 136-column basis: the Gram-Schmidt kernel's two-panels-per-lane variant
+    (more than 128 basis columns) and its shorter row slices."""
+    g = configs.msbm_n2000_k5_h2()["graph"]
+    lam, H, lab, info = solve_and_check(g, 5, prec, block=block, basis=136)
+    assert info["basis"] == 136
 
 
 def test_n50k_shape_scaled(built_lib):
