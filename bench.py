@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 / operator / e2e / CPU side measurements")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-graph batched measurement")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink n of the workload (profiling runs only)")
+    ap.add_argument("--cpu-child", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -276,65 +277,71 @@ def run_batched_main(args):
 
 
 # ---------------------------------------------------------------- oracle on the host cores
-def oracle_estimate(g, k, h, budget_s=12.0, step_model=None):
-    """Seconds per solve of the CPU oracle, from a bounded timed sample.
+class _StopCycles(Exception):
+    pass
 
-    The oracle (FP64 NumPy/SciPy, oracle/) is timed on the full graph: its
-    setup, operator applications (eq. asigma via Sec. 3.4) and full
-    reorthogonalisation at the average basis width; the step count is the
-    oracle's own thick-restart Lanczos count to tol 1e-6 on the same m-SBM
-    shape at n = 50,000 (step_model).  Returns (seconds per solve, sample text).
+
+def oracle_solve_timed(g, k, tol=1e-6, max_cycles=None, on_cycle=None):
+    """The CPU oracle's eigensolve (Algorithm 3 steps 1-3) on the full graph, timed.
+
+    Setup (operator_from_graph: degrees, L_n, C, the C^T C factor, sigma) and
+    the oracle's own thick-restart Lanczos (m = max(2k, 20), two classical
+    Gram-Schmidt passes per step, FP64) to ||A x - lambda x|| <= tol sigma.
+    Cycle i's time runs from the end of cycle i-1's steps to the end of its
+    own (so it includes the previous restart).  max_cycles stops the solve
+    early (a bounded sample).  Returns a dict of times and counts, and the
+    operator and vectors when the solve finished.
     """
-    import numpy as np
-
+    from oracle.lanczos import thick_restart_lanczos
     from oracle.sfairsc import operator_from_graph
 
     t0 = time.perf_counter()
     op = operator_from_graph(g)
     t_setup = time.perf_counter() - t0
-    m = max(2 * k, 20)
-    jbar = (k + (m - k) // 2 + m) // 2
-    rng = np.random.default_rng(0)
-    w = rng.standard_normal(g.n)
-    reps = 0
-    t0 = time.perf_counter()
-    while reps < 3 or (time.perf_counter() - t0 < budget_s / 3 and reps < 50):
-        op.apply(w)
-        reps += 1
-    t_op = (time.perf_counter() - t0) / reps
-    V = rng.standard_normal((g.n, jbar))
-    reps2 = 0
-    t0 = time.perf_counter()
-    while reps2 < 2 or (time.perf_counter() - t0 < budget_s / 3 and reps2 < 50):
-        u = w
-        for _ in range(2):
-            c = V.T @ u
-            u = w - V @ c
-        reps2 += 1
-    t_re = (time.perf_counter() - t0) / reps2
-    Y = rng.standard_normal((jbar, k))
-    t0 = time.perf_counter()
-    V @ Y
-    t_restart = (time.perf_counter() - t0) * (m / jbar) * ((k + (m - k) // 2) / k)
-    matvecs, restarts = step_model
-    est = t_setup + matvecs * (t_op + t_re) + restarts * t_restart
-    sample = (f"oracle on the full graph: setup {t_setup:.2f}s, {reps} operator applications "
-              f"({t_op:.3f}s each), {reps2} CGS2 sweeps at width {jbar} ({t_re:.3f}s each), one restart "
-              f"product; scaled by the oracle's own Lanczos counts on the n=50,000 instance of this shape "
-              f"({matvecs} matvecs, {restarts} restarts)")
-    return est, sample
+    marks = [time.perf_counter()]
+    mv = [0]
+
+    def cb(cycle, matvecs):
+        marks.append(time.perf_counter())
+        mv[0] = matvecs
+        if on_cycle is not None:
+            on_cycle(cycle, marks[-1] - marks[-2])
+        if max_cycles is not None and cycle + 1 >= max_cycles:
+            raise _StopCycles()
+
+    done, lam, X, info = True, None, None, {}
+    try:
+        lam, X, info = thick_restart_lanczos(op.apply, g.n, k, tol=tol, anorm=op.sigma, seed=0, on_cycle=cb)
+    except _StopCycles:
+        done = False
+    t_end = time.perf_counter()
+    cycles = [b - a for a, b in zip(marks[:-1], marks[1:])]
+    return {"op": op, "lam": lam, "X": X, "done": done, "setup_s": t_setup, "cycle_s": cycles,
+            "tail_s": t_end - marks[-1], "solve_s": t_end - marks[0], "matvecs": info.get("matvecs", mv[0]),
+            "restarts": info.get("restarts", len(cycles) - 1)}
 
 
-def oracle_step_model(name, k):
-    """The oracle's matvec and restart counts to tol 1e-6 on the n = 50,000 instance of the workload's shape."""
-    from msbm import configs
-    from oracle.lanczos import thick_restart_lanczos
-    from oracle.sfairsc import operator_from_graph
+def oracle_kmeans_timed(H, k, full=True, sample_iters=3, iters_total=None):
+    """The oracle's seeded k-means (Algorithm 3 step 4) on the rows of H: k-means++
+    seeding and Lloyd assignments to convergence (full), or the seeding and
+    sample_iters assignments timed and scaled to iters_total assignments."""
+    import numpy as np
 
-    c = configs.BUILDERS[name](scale=0.05) if name != "msbm_n2000_k5_h2" else configs.BUILDERS[name]()
-    op = operator_from_graph(c["graph"])
-    _, _, info = thick_restart_lanczos(op.apply, op.n, k, tol=1e-6, anorm=op.sigma, seed=0)
-    return info["matvecs"], info["restarts"]
+    from oracle.kmeans import kmeanspp, lloyd
+
+    X32 = np.ascontiguousarray(np.asarray(H, dtype=np.float64).astype(np.float32))
+    t0 = time.perf_counter()
+    seeds = kmeanspp(X32, k, 0, 0)
+    t_seed = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _, _, iters = lloyd(X32, X32[seeds].astype(np.float64), 100 if full else sample_iters)
+    t_lloyd = time.perf_counter() - t0
+    if full:
+        return t_seed + t_lloyd, iters, f"seeding {t_seed:.1f}s + {iters} Lloyd assignments {t_lloyd:.1f}s"
+    per = t_lloyd / iters
+    est = t_seed + per * iters_total
+    return est, iters_total, (f"seeding {t_seed:.1f}s + {iters} Lloyd assignments timed ({per:.2f}s each), "
+                              f"x {iters_total} assignments (the count of the same algorithm on the same H)")
 
 
 def host_threads():
@@ -344,34 +351,262 @@ def host_threads():
         return os.cpu_count()
 
 
+def oracle_single_thread_child(args):
+    """--cpu-child FILE: the oracle's setup and first two Lanczos cycles on one thread
+    (BLAS threads pinned to 1 by the parent's environment) on the graph saved in FILE;
+    prints one JSON line."""
+    import numpy as np
+
+    from msbm import Graph
+
+    d = np.load(args.cpu_child)
+    g = Graph(d["row_ptr"], d["col_idx"], d["values"], d["groups"], d["groups"] * 0, int(d["h"]), int(d["k"]))
+    r = oracle_solve_timed(g, int(d["k"]), tol=1e-6, max_cycles=2)
+    print(json.dumps({"setup_s": r["setup_s"], "cycle_s": r["cycle_s"]}), flush=True)
+
+
+def oracle_single_thread(g, k, cycles_total):
+    """Seconds per solve of the oracle on one host thread: setup and the first two cycles
+    timed in a child process with OMP/OPENBLAS/MKL threads = 1, the remaining cycles
+    at the second cycle's time (every later cycle does the same m - K steps)."""
+    import tempfile
+
+    import numpy as np
+
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    with tempfile.TemporaryDirectory() as tmp:
+        path = os.path.join(tmp, "graph.npz")
+        np.savez(path, row_ptr=g.row_ptr, col_idx=g.col_idx, values=g.values, groups=g.groups, h=g.h, k=k)
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-child", path],
+                           capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        return None, f"single-thread child failed: {r.stderr[-300:]}"
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    cyc = d["cycle_s"]
+    later = cyc[1] if len(cyc) > 1 else cyc[0]
+    est = d["setup_s"] + cyc[0] + later * max(0, cycles_total - 1)
+    return est, (f"one thread: setup {d['setup_s']:.1f}s, cycle 1 {cyc[0]:.1f}s, cycle 2 {later:.1f}s timed; "
+                 f"x {cycles_total} cycles of the all-core solve of the same graph")
+
+
 # ---------------------------------------------------------------- arms
 def run_reference(args):
+    """The CPU oracle on the host cores, on the same workload (no GPU).
+
+    A step is one restart cycle of the oracle's thick-restart Lanczos on the
+    full graph (a bounded sample of a few seconds).  Solves run back to back
+    cycle by cycle: W warm-up cycles, then K timed cycles; a solve that is
+    still running then continues to convergence, so at least one complete
+    solve is measured.  value = setup + every cycle of one complete solve +
+    embedding + the oracle's k-means to convergence on its H: a measured
+    time, nothing extrapolated."""
+    import numpy as np
+
     world, rank, _ = dist_env()
     if rank != 0:
         return
+    from oracle.sfairsc import embed
+
     c = load_workload(args.workload)
     g, k, h = c["graph"], c["k"], c["h"]
-    model = oracle_step_model(args.workload, k)
-    for _ in range(args.warmup):
-        oracle_estimate(g, k, h, budget_s=3.0, step_model=model)
-    vals = []
+    timed = []
+    state = {"cycle": 0}
+
+    def on_cycle(cycle, dt):
+        state["cycle"] += 1
+        if state["cycle"] > args.warmup and len(timed) < args.steps:
+            timed.append(dt)
+
+    solves = []
+    while True:
+        r = oracle_solve_timed(g, k, tol=1e-6, on_cycle=on_cycle)
+        solves.append(r)
+        if len(timed) >= args.steps:
+            break
+    first = solves[0]
     t0 = time.perf_counter()
-    sample = ""
-    for _ in range(args.steps):
-        v, sample = oracle_estimate(g, k, h, budget_s=6.0, step_model=model)
-        vals.append(v)
-    wall = time.perf_counter() - t0
-    value = statistics.median(vals)
+    H = embed(first["op"], first["X"])
+    t_embed = time.perf_counter() - t0
+    t_km, iters, km_text = oracle_kmeans_timed(H, k, full=True)
+    solve_s = statistics.median(x["setup_s"] + x["solve_s"] for x in solves)
+    value = solve_s + t_embed + t_km
     cores = host_threads()
+    sample = (f"oracle (FP64 NumPy/SciPy) on the full graph, {cores} host threads: {len(solves)} complete "
+              f"solve(s) to 1e-6 sigma, setup {first['setup_s']:.1f}s + {len(first['cycle_s'])} Lanczos cycles "
+              f"{first['solve_s']:.1f}s ({first['matvecs']} matvecs, {first['restarts']} restarts); embedding "
+              f"{t_embed:.2f}s; k-means: {km_text}; a step = one Lanczos cycle")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "s/solve", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall * 1e3 / max(args.steps, 1),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(timed) * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "n": g.n, "nnz": g.nnz, "k": k, "h": h, "parallelism": "host cores"},
-        "cpu_baseline": {"value": value, "unit": "s/solve", "cores": cores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "s/solve", "cores": cores, "kind": "oracle", "sample": sample,
+                         "matvecs": first["matvecs"], "restarts": first["restarts"]},
         "e2e": {"value": value, "unit": "s/solve", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def time_operator(B, s, dev, stream, g, s_v, s_x, nvecs, peak, reps=50):
+    """Median-free mean device time of back-to-back sfairsc_apply_operator calls (CUDA
+    events on the launching stream, 5 untimed first), and its algorithmic GB/s."""
+    import torch
+
+    out = {}
+    for nv in nvecs:
+        Wc = torch.randn(nv, g.n, device=dev, dtype=s.vec_dtype)
+        O = torch.empty_like(Wc)
+        for _ in range(5):
+            B.sfairsc_apply_operator(s.ctx, Wc.data_ptr(), O.data_ptr(), nv)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a0.record(stream)
+        for _ in range(reps):
+            B.sfairsc_apply_operator(s.ctx, Wc.data_ptr(), O.data_ptr(), nv)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        oms = a0.elapsed_time(a1) / reps
+        ob = operator_bytes(g.n, g.nnz, s_v, s_x, nv)
+        out[f"nvec{nv}"] = {"us": oms * 1e3, "achieved_gbs": ob / (oms * 1e6), "frac": ob / (oms * 1e6) / peak,
+                            "bytes": ob}
+    return out
+
+
+def h_sweep(FairSC, B, dev, stream, g, rp, ci, v, k, h, args, s_v, s_x, peak):
+    """Solve time of the same graph with its h groups merged to fewer (h = 1 is plain SC)."""
+    import torch
+
+    out = []
+    for hh in (1, 2, 5, h):
+        grp = torch.as_tensor((g.groups % hh) if hh > 1 else g.groups * 0, dtype=torch.int32, device=dev)
+        s = FairSC(rp, ci, v, grp, k=k, h=hh, prec=args.prec, block=args.block, profile=1)
+        s.solve(want_labels=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, _, inf = s.solve(want_labels=False)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        op = time_operator(B, s, dev, stream, g, s_v, s_x, (args.block,), peak, reps=20)[f"nvec{args.block}"]
+        s.close()
+        out.append({"h": hh, "solve_s": t, "matvecs": inf["matvecs"], "restarts": inf["restarts"],
+                    "ms_operator_total": inf["ms_operator"], "ms_orth_total": inf["ms_orth"],
+                    "operator_us": op["us"], "max_resid": inf["max_resid"]})
+    base = out[0]["solve_s"]
+    for r in out:
+        r["vs_sc"] = r["solve_s"] / base
+    return {"graph": "msbm_n1m_k50_h10 edges; groups merged as g mod h (h = 1: plain SC)", "prec": args.prec,
+            "block": args.block, "rows": out}
+
+
+def backward_bench(dev, peak):
+    """The differentiation form on the n = 200,000, k = 10, h = 4 Gaussian-weight workload: forward
+    solve time (MIXED) and the SDDMM backward (weights and bandwidth) time and algorithmic GB/s."""
+    import numpy as np
+    import torch
+
+    from msbm import configs
+    from paper_2210_16435_gb300.solver import FairSC
+
+    c = configs.msbm_n200k_k10_h4_gauss()
+    g, k, h, bw = c["graph"], c["k"], c["h"], c["bandwidth"]
+    T = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    rp, ci, v, gr = T(g.row_ptr, torch.int32), T(g.col_idx, torch.int32), T(g.values, torch.float32), \
+        T(g.groups, torch.int32)
+    s = FairSC(rp, ci, v, gr, k=k, h=h, prec="mixed")
+    s.solve(want_labels=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lam, _, _, inf = s.solve(want_labels=False)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    gl = torch.ones(k, dtype=torch.float64, device=dev)
+    for _ in range(3):
+        s.backward(gl, bw)
+    stream = torch.cuda.current_stream()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    torch.cuda.synchronize()
+    a0.record(stream)
+    for _ in range(reps):
+        s.backward(gl, bw)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    ms = a0.elapsed_time(a1) / reps
+    s.close()
+    # stored entries: column index + FP32 weight read, FP64 gradient written; H rows read once per row
+    bytes_ = g.nnz * (4 + 4) + g.n * k * 8 + g.nnz * 8 + 4 * (g.n + 1)
+    gbs = bytes_ / (ms * 1e6)
+    return {"workload": "msbm_n200k_k10_h4_gauss", "n": g.n, "nnz": g.nnz, "k": k, "forward_solve_s": t_fwd,
+            "forward_restarts": inf["restarts"], "backward_ms": ms, "backward_bytes": bytes_,
+            "achieved_gbs": gbs, "frac": gbs / peak,
+            "fd_check": "tests/test_gpu_backward.py::test_differentiation_workload_full_size"}
+
+
+def cpu_baseline(args, c, FairSC, rp, ci, v, gr, kw):
+    """The oracle on the host cores at the bench workload: setup + its own Lanczos to
+    1e-6 sigma (complete, timed, all threads) + embedding + k-means (seeding and three
+    Lloyd assignments timed on the library's H, scaled to the assignment count of the
+    identical k-means on that H); and the same on one thread (first two cycles timed)."""
+    from oracle.sfairsc import embed
+
+    g, k = c["graph"], c["k"]
+    cores = host_threads()
+    r = oracle_solve_timed(g, k, tol=1e-6)
+    t0 = time.perf_counter()
+    embed(r["op"], r["X"])
+    t_embed = time.perf_counter() - t0
+    s = FairSC(rp, ci, v, gr, **dict(kw, profile=0))
+    _, H, _, inf = s.solve()
+    s.close()
+    t_km, _, km_text = oracle_kmeans_timed(H.cpu().numpy(), k, full=False, sample_iters=3,
+                                           iters_total=max(1, inf["kmeans_iters"]))
+    value = r["setup_s"] + r["solve_s"] + t_embed + t_km
+    out = {"value": value, "unit": "s/solve", "cores": cores, "kind": "oracle",
+           "sample": (f"complete oracle solve of the full graph on {cores} host threads: setup {r['setup_s']:.1f}s, "
+                      f"{len(r['cycle_s'])} Lanczos cycles {r['solve_s']:.1f}s ({r['matvecs']} matvecs, "
+                      f"{r['restarts']} restarts) to 1e-6 sigma; embedding {t_embed:.2f}s; k-means: {km_text}"),
+           "matvecs": r["matvecs"], "restarts": r["restarts"], "setup_s": r["setup_s"], "solve_s": r["solve_s"],
+           "kmeans_s": t_km}
+    st, st_text = oracle_single_thread(g, k, len(r["cycle_s"]))
+    if st is not None:
+        out["single_thread"] = {"value": st + t_embed + t_km, "unit": "s/solve", "cores": 1, "kind": "oracle",
+                                "sample": st_text + "; embedding and k-means as above (single-threaded NumPy)"}
+    return out
+
+
+def fairsc_c1(FairSC, dev):
+    """Context for the paper's FairSC-vs-s-FairSC comparison (Exp. 1) at n = 2,000, k = 5, h = 2:
+    dense FairSC (Algorithm 2) and the sparse s-FairSC oracle on the host, and the library's
+    FP64 solve on the GPU."""
+    import numpy as np
+    import torch
+
+    from msbm import configs
+    from oracle import fairsc
+    from oracle.sfairsc import operator_from_graph, smallest_eigenpairs
+
+    c = configs.msbm_n2000_k5_h2()
+    g, k, h = c["graph"], c["k"], c["h"]
+    W = g.to_scipy()
+    t0 = time.perf_counter()
+    fairsc.fairsc_dense(W, g.groups, h, k)
+    t_dense = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    op = operator_from_graph(g)
+    smallest_eigenpairs(op, k, tol=1e-6, method="lanczos")
+    t_sparse = time.perf_counter() - t0
+    T = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    args = (T(g.row_ptr, torch.int32), T(g.col_idx, torch.int32), T(g.values, torch.float64), T(g.groups, torch.int32))
+    FairSC(*args, k=k, h=h, prec="fp64").close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s = FairSC(*args, k=k, h=h, prec="fp64")
+    s.solve(want_labels=False)
+    s.close()
+    torch.cuda.synchronize()
+    t_gpu = time.perf_counter() - t0
+    return {"workload": "msbm_n2000_k5_h2", "fairsc_dense_host_s": t_dense, "sfairsc_oracle_host_s": t_sparse,
+            "sfairsc_gpu_fp64_s": t_gpu, "host_threads": host_threads()}
 
 
 def run_ours(args):
@@ -481,35 +716,29 @@ def run_ours(args):
     if rank == 0 and not args.no_extras:
         # standalone fused operator on the workload (the metric's operator GB/s), b = 1 and 4
         s = FairSC(rp, ci, v, gr, k=k, h=h, prec=args.prec, block=args.block)
-        opx = {}
-        for nv in (1, 4):
-            Wc = torch.randn(nv, g.n, device=dev, dtype=s.vec_dtype)
-            O = torch.empty_like(Wc)
-            for _ in range(5):
-                B.sfairsc_apply_operator(s.ctx, Wc.data_ptr(), O.data_ptr(), nv)
-            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            a0.record(stream)
-            reps = 50
-            for _ in range(reps):
-                B.sfairsc_apply_operator(s.ctx, Wc.data_ptr(), O.data_ptr(), nv)
-            a1.record(stream)
-            torch.cuda.synchronize()
-            oms = a0.elapsed_time(a1) / reps
-            ob = operator_bytes(g.n, g.nnz, s_v, s_x, nv)
-            opx[f"nvec{nv}"] = {"us": oms * 1e3, "achieved_gbs": ob / (oms * 1e6), "frac": ob / (oms * 1e6) / peak,
-                                "bytes": ob}
+        opx = time_operator(B, s, dev, stream, g, s_v, s_x, (1, 4), peak)
         s.close()
         line["operator"] = opx
-        # plain FP64 GPU path (block 1) on the same graph, once
-        t0 = time.perf_counter()
-        s = FairSC(rp, ci, v, gr, k=k, h=h, prec="fp64", block=1)
-        _, _, _, i64 = s.solve()
-        torch.cuda.synchronize()
-        line["fp64_block1_solve_s"] = time.perf_counter() - t0
-        line["fp64_block1_info"] = {"restarts": i64["restarts"], "matvecs": i64["matvecs"],
-                                    "max_resid": i64["max_resid"]}
+        # plain FP64 GPU path on the same graph, block 1 and block 4 (block 4 isolates the precision effect)
+        for blk in (1, 4):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s = FairSC(rp, ci, v, gr, k=k, h=h, prec="fp64", block=blk)
+            _, _, _, i64 = s.solve()
+            torch.cuda.synchronize()
+            line[f"fp64_block{blk}_solve_s"] = time.perf_counter() - t0
+            line[f"fp64_block{blk}_info"] = {"restarts": i64["restarts"], "matvecs": i64["matvecs"],
+                                             "max_resid": i64["max_resid"], "ms_final": i64["ms_final"]}
+            s.close()
+        # the FP64 operator alone (the final residual check and the plain FP64 path use it)
+        s = FairSC(rp, ci, v, gr, k=k, h=h, prec="fp64", block=4)
+        line["operator_fp64"] = time_operator(B, s, dev, stream, g, VDT_BYTES[c["value_dtype"]], 8, (1, 4), peak)
         s.close()
+        # s-FairSC against plain SC on the same graph (the paper's overhead question, Exp. 1/4, App. C):
+        # the same W with its groups merged to h = 5, 2 and 1 (h = 1: no fairness constraint, Algorithm 1)
+        line["h_sweep"] = h_sweep(FairSC, B, dev, stream, g, rp, ci, v, k, h, args, s_v, s_x, peak)
+        # differentiation form: gradient of the sum of the 10 smallest eigenvalues at n = 200,000
+        line["backward"] = backward_bench(dev, peak)
         # end to end through the C ABI with host buffers: copies inside the timed region
         hp = [torch.as_tensor(np.ascontiguousarray(a), dtype=dt).pin_memory()
               for a, dt in ((g.row_ptr, torch.int32), (g.col_idx, torch.int32), (g.values, vdt),
@@ -529,12 +758,10 @@ def run_ours(args):
         # batched form (256 graphs, one launch) against sequential single-graph solves
         if not args.no_batched:
             line["batched"] = batched_extra(dev, peak)
-        # the CPU oracle on the host cores (bounded sample, scaled to seconds per solve)
+        # the CPU oracle on the host cores: a complete, timed solve of the same graph
         if world == 1:
-            model = oracle_step_model(args.workload, k)
-            est, sample = oracle_estimate(g, k, h, budget_s=15.0, step_model=model)
-            line["cpu_baseline"] = {"value": est, "unit": "s/solve", "cores": host_threads(), "kind": "oracle",
-                                    "sample": sample}
+            line["cpu_baseline"] = cpu_baseline(args, c, FairSC, rp, ci, v, gr, kw)
+            line["fairsc_c1"] = fairsc_c1(FairSC, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -543,6 +770,9 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.cpu_child:
+        oracle_single_thread_child(args)
+        return
     if args.workload == "msbm_batch256" and args.impl != "reference":
         run_batched_main(args)
         return

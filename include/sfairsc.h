@@ -50,7 +50,7 @@ extern "C" {
 #define SFAIRSC_API
 #endif
 
-#define SFAIRSC_ABI_VERSION 1
+#define SFAIRSC_ABI_VERSION 2
 #define SFAIRSC_MAX_GROUPS 32   /* h <= 32: groups are reduced with one warp lane each */
 #define SFAIRSC_MAX_BLOCK 4     /* Krylov block size b in 1..4 */
 
@@ -92,7 +92,14 @@ typedef struct {
   int32_t kmeans_max_iter; /* Lloyd assignments per replicate; default 100 */
   int32_t validate;        /* 0: none, 1: structure checks (default), 2: also symmetry (sorted columns) */
   int32_t profile;         /* 1: time the operator and orthogonalisation kernels with CUDA events (info.ms_*) */
-  int32_t reserved[8];
+  int32_t wait_limit_us;   /* bound of every device-side wait (grid barriers, copy completions) in
+                              microseconds; a wait that runs out sets an error word, the kernel returns
+                              and the call reports DEVICE_TIMEOUT; 0 => 2,000,000 (2 s) */
+  int32_t fault_inject;    /* testing hook, 0 normally.  1: the first operator launch of the next
+                              sfairsc_solve / sfairsc_apply_operator call waits on a device flag that
+                              nothing sets, so that call ends in DEVICE_TIMEOUT after wait_limit_us
+                              (no fault, no hang); the hook is then cleared and later calls run normally */
+  int32_t reserved[6];
 } sfairsc_opts;
 
 typedef struct {
@@ -118,6 +125,9 @@ typedef struct {
   float ms_restart;        /* with opts.profile: device time of the thick-restart GEMMs */
   float ms_host_eig;       /* host time of the projected eigenproblems (one per restart) */
   float ms_final;          /* device time of the final FP64 check, projection and embedding */
+  int32_t host_eig_fallbacks; /* projected eigenproblems whose QR iteration hit its sweep limit and were
+                                 solved again by cyclic Jacobi */
+  int32_t reserved[7];
 } sfairsc_info;
 
 typedef struct sfairsc_ctx sfairsc_ctx;
@@ -226,12 +236,11 @@ SFAIRSC_API int sfairsc_backward(sfairsc_ctx* ctx, const double* grad_lambda, do
 /*
  * One application of L_n^sigma (same result as sfairsc_apply_operator in
  * MIXED precision) that allocates no memory at all.  The paper has no
- * counterpart: this exists for callers that cannot call cudaMalloc -- code
- * that runs while another component is capturing a CUDA graph, plug-ins
- * inside runtimes that own the device allocator or forbid allocation after
- * start-up, and fixed-budget embedded or real-time deployments.  No context
- * is needed: degrees, D^{-1/2}, the C^T C factor and sigma = ||L_n||_1 are
- * recomputed on every call from the inputs.
+ * counterpart.  It serves callers that cannot call cudaMalloc: plug-ins that
+ * run inside a host runtime which owns the device allocator or refuses new
+ * allocations once it has started, and deployments whose device memory budget
+ * is fixed at start-up.  No context is needed: degrees, D^{-1/2}, the C^T C
+ * factor and sigma = ||L_n||_1 are recomputed on every call from the inputs.
  *
  * n, nnz, row_ptr, col_idx   CSR of the symmetric W as in sfairsc_create
  * values                      FP32 weights; group_labels int32 in [0, h)
@@ -246,7 +255,8 @@ SFAIRSC_API int sfairsc_backward(sfairsc_ctx* ctx, const double* grad_lambda, do
  * share the array and it keeps the last call's contents (each call clears the
  * words that must start at zero): calls that overlap on the GPU race, so do
  * not run two at once on one device.  Calls from different host threads are
- * serialised.  Returns after out is written.
+ * serialised.  Each call waits on cuda_stream for its set-up reductions and
+ * returns after out is written.
  * Errors: INVALID_ARG (null or host pointer, bad size), UNSUPPORTED (n or h
  * above the limits), BAD_CSR, ISOLATED_VERTEX, EMPTY_GROUP, NONFINITE,
  * DEVICE_TIMEOUT, CUDA.

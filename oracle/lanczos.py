@@ -14,9 +14,12 @@ import numpy as np
 
 
 def thick_restart_lanczos(apply, n: int, k: int, m: int | None = None, tol: float = 1e-12, anorm: float = 1.0,
-                          seed: int = 0, max_restarts: int = 500):
+                          seed: int = 0, max_restarts: int = 500, v0=None, on_cycle=None):
     """k smallest eigenpairs of the symmetric operator `apply` (ascending).
 
+    v0: start vector (default: a seeded Gaussian vector).
+    on_cycle: called as on_cycle(cycle, matvecs) after each restart cycle's
+    Lanczos steps (a timing hook for the benchmark; it changes nothing).
     Returns (eigenvalues[k], X[n, k], info dict).
     """
     if m is None:
@@ -26,7 +29,7 @@ def thick_restart_lanczos(apply, n: int, k: int, m: int | None = None, tol: floa
         m = min(n, k + 1)
     V = np.zeros((n, m + 1))
     T = np.zeros((m + 1, m + 1))
-    v = np.random.default_rng(seed).standard_normal(n)
+    v = np.random.default_rng(seed).standard_normal(n) if v0 is None else np.asarray(v0, dtype=np.float64)
     V[:, 0] = v / np.linalg.norm(v)
     j0 = 0
     matvecs = 0
@@ -49,6 +52,8 @@ def thick_restart_lanczos(apply, n: int, k: int, m: int | None = None, tol: floa
                 V[:, j + 1] = w / beta_dir
             else:
                 V[:, j + 1] = w / beta
+        if on_cycle is not None:
+            on_cycle(restart, matvecs)
         Tm = np.triu(T[:m, :m]) + np.triu(T[:m, :m], 1).T
         theta, Y = np.linalg.eigh(Tm)
         resid = np.abs(beta * Y[m - 1, :])

@@ -126,6 +126,8 @@ struct sfairsc_ctx {
   int32_t* labels_d = nullptr;
   std::vector<double> lam_h;
   bool solved = false;
+  bool fault_pending = false;
+  bool shift_found = false;    // the last final check met a Ritz vector in range(C)  // opts.fault_inject: the next operator launch waits on a flag nothing sets
   // live kernel timing (opts.profile) and launch counting
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_op, ev_orth, ev_restart;
@@ -366,6 +368,10 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   o.barrier = reinterpret_cast<unsigned long long*>(c->barrier);
   o.err = c->err;
   o.work = c->barrier + 4;
+  const unsigned long long wait_ns =
+      c->opts.wait_limit_us > 0 ? (unsigned long long)c->opts.wait_limit_us * 1000ull : 2000000000ull;
+  o.wait_ns = wait_ns;
+  c->fault_pending = c->opts.fault_inject != 0;
   c->op64 = o;
   c->op64.val = c->val_orig;
   c->op64.val_dtype = c->vdt_orig;
@@ -424,6 +430,7 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   q.err = c->err;
   q.brk_step = c->brk_step;
   q.sweeps = c->sweeps;
+  q.wait_ns = wait_ns;
   check_cuda(cudaMallocHost((void**)&c->Hh, sizeof(double) * c->ldh * m), "pinned allocation");
   check_cuda(cudaMallocHost((void**)&c->Yh, sizeof(double) * m * m), "pinned allocation");
   check_cuda(cudaMallocHost(&c->Ystage, sizeof(double) * m * m), "pinned allocation");
@@ -459,7 +466,11 @@ void check_err_word(sfairsc_ctx* c) {
 
 void apply_op(sfairsc_ctx* c, bool fp64, const void* w, int64_t wrs, int64_t wcs, void* out, int64_t ors, int64_t ocs,
               int nvec) {
-  const OpPlan& p = fp64 ? c->op64 : c->op;
+  OpPlan p = fp64 ? c->op64 : c->op;
+  if (c->fault_pending) {  // testing hook: word 12 of the counter block is zero and nothing writes it
+    p.stall_flag = c->barrier + 12;
+    c->fault_pending = false;
+  }
   const bool timed = c->opts.profile && !fp64;
   cudaEvent_t a = nullptr, b = nullptr;
   if (timed) {
@@ -571,8 +582,21 @@ double final_check(sfairsc_ctx* c, int mv, const std::vector<double>& T, std::ve
       xay[i] += st[((size_t)b * k + i) * 3 + 0];
       xx[i] += st[((size_t)b * k + i) * 3 + 1];
     }
+  // A unit Ritz vector that keeps less than half of its norm under P lies
+  // mostly in range(C), the eigenspace of sigma (Prop. 3.2): sigma is not above
+  // the wanted eigenvalues (Prop. 3.3).  Its eigenvalue is reported as sigma.
   c->lam_h.assign(k, 0.0);
-  for (int i = 0; i < k; ++i) c->lam_h[i] = xay[i] / xx[i];
+  c->shift_found = false;
+  std::vector<char> in_range_c(k, 0);
+  for (int i = 0; i < k; ++i) {
+    if (xx[i] < 0.25) {
+      in_range_c[i] = 1;
+      c->shift_found = true;
+      xay[i] = c->sigma;
+      xx[i] = 1.0;
+    }
+    c->lam_h[i] = xay[i] / xx[i];
+  }
   check_cuda(cudaMemcpyAsync(c->lam_d, c->lam_h.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s), "h2d");
   launch_column_resid(n, k, c->X64, c->AX64, c->lam_d, c->stat_partial, c->stat_blocks, s);
   std::vector<double> rp((size_t)c->stat_blocks * k);
@@ -580,6 +604,7 @@ double final_check(sfairsc_ctx* c, int mv, const std::vector<double>& T, std::ve
   check_cuda(cudaStreamSynchronize(s), "residual");
   double maxres = 0.0;
   for (int i = 0; i < k; ++i) {
+    if (in_range_c[i]) continue;
     double r2 = 0.0;
     for (int b = 0; b < c->stat_blocks; ++b) r2 += rp[(size_t)b * k + i];
     maxres = std::max(maxres, std::sqrt(r2 / xx[i]) / c->sigma);
@@ -595,7 +620,7 @@ int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* label
   inf.sigma = c->sigma;
   Timer tsolve(s);
   c->n_launches = 0;
-  int n_op = 0, n_orth = 0, orth_cols = 0;
+  int n_op = 0, n_orth = 0, orth_cols = 0, eig_fallbacks = 0;
   float ms_op = 0.f, ms_orth = 0.f, ms_restart = 0.f;
   double ms_eig = 0.0;
   check_cuda(cudaMemsetAsync(c->sweeps, 0, sizeof(int), s), "memset");
@@ -643,7 +668,14 @@ int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* label
       }
     {
       const auto t0 = std::chrono::steady_clock::now();
-      host_symmetric_eig(mv, T.data(), theta.data());
+      const std::vector<double> T0 = T;
+      if (!host_symmetric_eig(mv, T.data(), theta.data())) {
+        // the QR iteration hit its sweep limit: solve the projected problem again by Jacobi
+        T = T0;
+        if (!host_symmetric_eig_jacobi(mv, T.data(), theta.data()))
+          fail(SFAIRSC_ERR_NONFINITE, "the projected matrix holds a non-finite entry");
+        ++eig_fallbacks;
+      }
       ms_eig += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
     for (int i = 0; i < mv; ++i) {
@@ -663,7 +695,7 @@ int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* label
       Timer tfin(s);
       maxres = final_check(c, mv, T, xx);
       inf.ms_final += tfin.stop(s);
-      if (maxres <= c->opts.tol || out_of_restarts) {
+      if (maxres <= c->opts.tol || out_of_restarts || c->shift_found) {
         converged = maxres <= c->opts.tol;
         break;
       }
@@ -740,6 +772,7 @@ int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* label
   inf.ms_restart = ms_restart;
   inf.ms_host_eig = (float)ms_eig;
   inf.n_operator = n_op;
+  inf.host_eig_fallbacks = eig_fallbacks;
   inf.n_orth = n_orth;
   inf.orth_cols = orth_cols;
   {
@@ -880,7 +913,8 @@ int sfairsc_create(sfairsc_ctx** out, int64_t n, int64_t nnz, const int32_t* row
   sfairsc_opts_default(&c->opts);
   if (opts) c->opts = *opts;
   if (!(c->opts.tol > 0.0) || c->opts.max_restarts < 0 || c->opts.block < 1 || c->opts.block > SFAIRSC_MAX_BLOCK ||
-      c->opts.kmeans_n_init < 1 || c->opts.kmeans_max_iter < 1 || (c->opts.prec != 0 && c->opts.prec != 1)) {
+      c->opts.kmeans_n_init < 1 || c->opts.kmeans_max_iter < 1 || (c->opts.prec != 0 && c->opts.prec != 1) ||
+      c->opts.wait_limit_us < 0 || (c->opts.fault_inject != 0 && c->opts.fault_inject != 1)) {
     g_last_error = "invalid options";
     return SFAIRSC_ERR_INVALID_ARG;
   }

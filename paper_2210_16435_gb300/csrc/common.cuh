@@ -209,6 +209,28 @@ __device__ __forceinline__ bool grid_sync(GridBarrier bar, unsigned* err, unsign
   return ok_s != 0;
 }
 
+// Bounded wait of the whole CTA for *flag to become nonzero (a fault-injection
+// hook: the caller passes a word that nothing sets).  Thread 0 polls; after
+// limit_ns it sets kErrBarrierTimeout in *err.  Returns true if the flag was seen.
+__device__ __forceinline__ bool wait_flag(const unsigned* flag, unsigned* err, unsigned long long limit_ns) {
+  __shared__ int seen_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int seen = 1;
+    const unsigned long long t0 = globaltimer_ns();
+    while (ld_acquire_gpu(flag) == 0u) {
+      if (globaltimer_ns() - t0 > limit_ns) {
+        atomicOr(err, kErrBarrierTimeout);
+        seen = 0;
+        break;
+      }
+    }
+    seen_s = seen;
+  }
+  __syncthreads();
+  return seen_s != 0;
+}
+
 }  // namespace sfairsc
 
 namespace sfairsc {

@@ -11,6 +11,7 @@
 // Rows are independent, so blocks of rows go to a few host threads.
 #include <algorithm>
 #include <cmath>
+#include <limits>
 #include <numeric>
 #include <thread>
 #include <vector>
@@ -28,7 +29,7 @@ struct Rotation {
 
 }  // namespace
 
-void host_symmetric_eig(int m, double* A, double* w) {
+bool host_symmetric_eig(int m, double* A, double* w, int max_sweeps) {
   // A: m x m column-major symmetric; on exit its columns are the eigenvectors.
   auto a = [&](int i, int j) -> double& { return A[(size_t)j * m + i]; };
 
@@ -84,7 +85,8 @@ void host_symmetric_eig(int m, double* A, double* w) {
   rot.reserve((size_t)8 * m * m);
   int hi = m - 1;
   int guard = 0;
-  while (hi > 0 && guard < 60 * m) {
+  const int guard_limit = max_sweeps < 0 ? 60 * m : max_sweeps;
+  while (hi > 0 && guard < guard_limit) {
     if (std::fabs(e[hi - 1]) <= eps * (std::fabs(d[hi - 1]) + std::fabs(d[hi]))) {
       e[hi - 1] = 0.0;
       --hi;
@@ -191,6 +193,65 @@ void host_symmetric_eig(int m, double* A, double* w) {
     rows(lo, hi2);
     for (auto& th : pool) th.join();
   }
+  return hi <= 0;
+}
+
+bool host_symmetric_eig_jacobi(int m, double* A, double* w) {
+  // Cyclic Jacobi (Golub and Van Loan, Sec. 8.5): sweep over all (p, q) pairs,
+  // zeroing a_pq by a plane rotation chosen with |angle| <= pi/4, until the
+  // off-diagonal mass is below eps^2 of the total.  V accumulates the rotations.
+  auto a = [&](int i, int j) -> double& { return A[(size_t)j * m + i]; };
+  for (size_t i = 0; i < (size_t)m * m; ++i)
+    if (!std::isfinite(A[i])) return false;
+  std::vector<double> V((size_t)m * m, 0.0);
+  for (int i = 0; i < m; ++i) V[(size_t)i * m + i] = 1.0;
+  const double eps = std::numeric_limits<double>::epsilon();
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int j = 0; j < m; ++j)
+      for (int i = 0; i < m; ++i) {
+        const double x = a(i, j) * a(i, j);
+        tot += x;
+        if (i != j) off += x;
+      }
+    if (off <= eps * eps * tot || off == 0.0) break;
+    for (int p = 0; p < m - 1; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        const double apq = a(p, q);
+        if (apq == 0.0) continue;
+        // tan of the rotation angle: t = sign(tau) / (|tau| + sqrt(1 + tau^2)), tau = (a_qq - a_pp) / (2 a_pq)
+        const double tau = (a(q, q) - a(p, p)) / (2.0 * apq);
+        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+        const double c = 1.0 / std::sqrt(1.0 + t * t), s = t * c;
+        for (int k = 0; k < m; ++k) {  // columns p, q: A <- A J
+          const double akp = a(k, p), akq = a(k, q);
+          a(k, p) = c * akp - s * akq;
+          a(k, q) = s * akp + c * akq;
+        }
+        for (int k = 0; k < m; ++k) {  // rows p, q: A <- J^T A
+          const double apk = a(p, k), aqk = a(q, k);
+          a(p, k) = c * apk - s * aqk;
+          a(q, k) = s * apk + c * aqk;
+        }
+        for (int k = 0; k < m; ++k) {
+          double* vp = &V[(size_t)p * m + k];
+          double* vq = &V[(size_t)q * m + k];
+          const double x = *vp, y = *vq;
+          *vp = c * x - s * y;
+          *vq = s * x + c * y;
+        }
+      }
+  }
+  std::vector<int> order(m);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int i, int j) { return a(i, i) < a(j, j); });
+  std::vector<double> d(m);
+  for (int i = 0; i < m; ++i) d[i] = a(i, i);
+  for (int c = 0; c < m; ++c) {
+    w[c] = d[order[c]];
+    for (int k = 0; k < m; ++k) A[(size_t)c * m + k] = V[(size_t)order[c] * m + k];
+  }
+  return true;
 }
 
 }  // namespace sfairsc

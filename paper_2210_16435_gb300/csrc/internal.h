@@ -66,6 +66,8 @@ struct OpPlan {
   unsigned long long* barrier = nullptr;  // grid barrier arrival counter (64-bit)
   unsigned* err = nullptr;
   unsigned* work = nullptr;    // 1 word: dynamic row-block counter of the SpMV
+  unsigned long long wait_ns = 2000000000ull;  // bound of every device-side wait
+  const unsigned* stall_flag = nullptr;  // non-null: the launch first waits for this word (never set) to become nonzero
 };
 
 // Launch out = L_n^sigma w for nvec vectors; element (r, v) of w is w[r*wrs + v*wcs]
@@ -106,6 +108,7 @@ struct OrthPlan {
   unsigned* err = nullptr;
   int* brk_step = nullptr;    // smallest step j whose new block lost rank (atomicMin)
   int* sweeps = nullptr;      // accumulates the number of passes over V
+  unsigned long long wait_ns = 2000000000ull;  // bound of every device-side wait
 };
 // Orthogonalise the B columns in U against V[:, 0:J] (CGS2), record the
 // coefficients in H[0:J, j:j+B], orthonormalise the block (CholQR), store it
@@ -154,8 +157,14 @@ struct KmeansResult {
 KmeansResult run_kmeans(int64_t n, int d, const double* X, int kc, uint64_t seed, int n_init, int max_iter,
                         int32_t* labels, double* centroids, cudaStream_t s);
 
-// Host FP64 symmetric eigensolver (Householder tridiagonalisation + implicit QL).
+// Host FP64 symmetric eigensolver (Householder tridiagonalisation + implicit QR).
 // A: m x m column-major symmetric (overwritten with eigenvectors), w: eigenvalues ascending.
-void host_symmetric_eig(int m, double* A, double* w);
+// Returns false when the QR iteration used up max_sweeps (default 60 m) before
+// every off-diagonal entry deflated: A and w then hold an unconverged result.
+bool host_symmetric_eig(int m, double* A, double* w, int max_sweeps = -1);
+// Cyclic Jacobi (FP64) for the same problem: always converges for finite
+// input; slower, the fallback when the QR iteration gives up.  Returns false
+// if A holds a non-finite entry.
+bool host_symmetric_eig_jacobi(int m, double* A, double* w);
 
 }  // namespace sfairsc

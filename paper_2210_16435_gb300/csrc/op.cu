@@ -44,6 +44,8 @@ struct OpArgs {
   GridBarrier bar;
   unsigned* err;
   unsigned* work;  // dynamic row-block counter of the SpMV phase
+  unsigned long long wait_ns;  // bound of every grid-barrier wait
+  const unsigned* stall;       // fault-injection hook: wait for this (never set) word first
 };
 
 template <typename VT, int B>
@@ -286,6 +288,7 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
   VT* coefAv = reinterpret_cast<VT*>(coefD + kMaxGroups * B);  // 32*B, in the vector type
 
   const int r0 = a.cta_rows[blockIdx.x], r1 = a.cta_rows[blockIdx.x + 1];
+  if (a.stall && !wait_flag(a.stall, a.err, a.wait_ns)) return;
 
   auto scale = [&](int r) -> VT { return a.normalized ? a.dinv[r] : VT(1); };
 
@@ -297,7 +300,7 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
 #pragma unroll
       for (int v = 0; v < B; ++v) x[v] *= sc;
     });
-    if (!grid_sync(a.bar, a.err)) return;
+    if (!grid_sync(a.bar, a.err, a.wait_ns)) return;
     // ---------------- phase B: a = (C^T C)^{-1} C^T w
     reduce_partials(a.partial, gridDim.x, P, scratch, tot);
     solve_groups<B>(tot, a.params, h, avec, coefA);
@@ -330,7 +333,7 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) *a.work = 0u;  // no CTA takes a block before the barrier
-  if (!grid_sync(a.bar, a.err)) return;
+  if (!grid_sync(a.bar, a.err, a.wait_ns)) return;
 
   // ---------------- phase C: t = L_n y, written to out
   // Warps take blocks of 4 row groups from a global counter (load balance
@@ -456,7 +459,7 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
   }
   if (!grouped) return;
   // t rows were written by any CTA: make them visible, then group sums over own rows (through L2)
-  if (!grid_sync(a.bar, a.err)) return;
+  if (!grid_sync(a.bar, a.err, a.wait_ns)) return;
   cta_group_sums<VT, B>(r0, r1, h, a.lab, red, a.partial, [&](int r, VT(&x)[B]) {
     const VT sc = scale(r);
     if (a.ocs == 1 && a.ors == B) {
@@ -468,7 +471,7 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
       for (int v = 0; v < B; ++v) x[v] = sc * __ldcg(a.out + r * a.ors + v * a.ocs);
     }
   });
-  if (!grid_sync(a.bar, a.err)) return;
+  if (!grid_sync(a.bar, a.err, a.wait_ns)) return;
 
   // ---------------- phase D: b = (C^T C)^{-1} C^T t; out = t - C (b - sigma a)
   reduce_partials(a.partial, gridDim.x, P, scratch, tot);
@@ -541,6 +544,8 @@ static void launch_t(const OpPlan& p, const void* w, int64_t wrs, int64_t wcs, v
   a.bar = GridBarrier{p.barrier};
   a.err = p.err;
   a.work = p.work;
+  a.wait_ns = p.wait_ns;
+  a.stall = p.stall_flag;
   const size_t smem = operator_smem_bytes(p.threads, p.h, B, sizeof(VT) == 8 ? VecType::F64 : VecType::F32);
   auto kern = fused_operator_kernel<VT, MT, B>;
   check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "operator smem attr");

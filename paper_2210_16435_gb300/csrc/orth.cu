@@ -249,6 +249,7 @@ struct OrthArgs {
   int* brk_step;
   int* sweeps;
   int J, j;
+  unsigned long long wait_ns;  // bound of every grid-barrier wait
 };
 
 // Sweep slices: SR consecutive rows of every panel V[:, 4p:4p+4] (p < np)
@@ -645,16 +646,16 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
     // sweep 1: c1 = V^T U and the input norms
     if (!sweep(0)) return;
     ++sweeps;
-    if (!grid_sync(a.bar, a.err)) return;
+    if (!grid_sync(a.bar, a.err, a.wait_ns)) return;
     reduce_owned(a.partial, kStride, gridDim.x, P, a.coef, scratch);
     if (a.j >= 0)
       for (int p = blockIdx.x; p < P; p += gridDim.x) a.H[(size_t)(p / B) + (size_t)a.ldh * (a.j + p % B)] = a.coef[p];
     reduce_all(a.partial, kStride, gridDim.x, kNormOff, B, unorm, scratch);
-    if (!grid_sync(a.bar, a.err)) return;
+    if (!grid_sync(a.bar, a.err, a.wait_ns)) return;
     // sweep 2: U -= V c1; c2 = V^T U; Gram
     if (!sweep(1)) return;
     ++sweeps;
-    if (!grid_sync(a.bar, a.err)) return;
+    if (!grid_sync(a.bar, a.err, a.wait_ns)) return;
     reduce_all(a.partial, kStride, gridDim.x, kGramOff, B * B, gram_s, scratch);
     if (threadIdx.x == 0) {
       again = 0;
@@ -666,17 +667,17 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
       reduce_owned(a.partial, kStride, gridDim.x, P, a.coef, scratch);
       if (a.j >= 0)
         for (int p = blockIdx.x; p < P; p += gridDim.x) a.H[(size_t)(p / B) + (size_t)a.ldh * (a.j + p % B)] += a.coef[p];
-      if (!grid_sync(a.bar, a.err)) return;
+      if (!grid_sync(a.bar, a.err, a.wait_ns)) return;
       // sweep 3: U -= V c2; Gram
       if (!sweep(2)) return;
       ++sweeps;
-      if (!grid_sync(a.bar, a.err)) return;
+      if (!grid_sync(a.bar, a.err, a.wait_ns)) return;
       reduce_all(a.partial, kStride, gridDim.x, kGramOff, B * B, gram_s, scratch);
     }
   } else {
     if (threadIdx.x < B) unorm[threadIdx.x] = 0.0;
     gram_rows(kGramOff, false);
-    if (!grid_sync(a.bar, a.err)) return;
+    if (!grid_sync(a.bar, a.err, a.wait_ns)) return;
     reduce_all(a.partial, kStride, gridDim.x, kGramOff, B * B, gram_s, scratch);
   }
   cholesky(R1, Rd1);
@@ -684,7 +685,7 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
   if (B > 1) {
     // Cholesky QR a second time: U <- U R1^{-1}, Gram again
     gram_rows(kGram2Off, true);
-    if (!grid_sync(a.bar, a.err)) return;
+    if (!grid_sync(a.bar, a.err, a.wait_ns)) return;
     reduce_all(a.partial, kStride, gridDim.x, kGram2Off, B * B, gram_s, scratch);
     if (threadIdx.x < B) unorm[threadIdx.x] = 0.0;
     __syncthreads();
@@ -774,6 +775,7 @@ static void orth_launch_t(const OrthPlan& p, int J, int j, cudaStream_t s) {
   a.sweeps = p.sweeps;
   a.J = J;
   a.j = j;
+  a.wait_ns = p.wait_ns;
   const size_t smem = orth_smem_bytes<VT, NC>();
   auto kern = orth_kernel<VT, B, NC>;
   check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "orth smem attr");

@@ -114,6 +114,26 @@ def test_n50k_shape_scaled(built_lib):
     solve_and_check(g, 20, "fp64", vdt=torch.float32)
 
 
+@pytest.mark.parametrize("block", [1, 4])
+def test_n50k_k20_h5_full_size(built_lib, block):
+    """m-SBM n = 50,000, k = 20, h = 5 at its stated size, FP32 values, mixed precision, against
+    the oracle's eigsh (tol 1e-13): eigenvalues, residuals, invariants, principal angles, and the
+    cluster balance of the library's labels against the oracle's k-means on the oracle's H."""
+    c = configs.msbm_n50k_k20_h5()
+    g, k, h = c["graph"], c["k"], c["h"]
+    op = operator_from_graph(g)
+    lref, Xref = smallest_eigenpairs(op, k + 1, tol=1e-13, method="eigsh")
+    d = problem.degrees(g.to_scipy())
+    Href = Xref / np.sqrt(d)[:, None]
+    lam, H, lab, info = solve_and_check(g, k, "mixed", block=block, vdt=torch.float32, ref=(lref, Href))
+    from oracle.sfairsc import sign_normalize
+
+    oref, _, _ = oracle_kmeans(sign_normalize(Xref[:, :k]) / np.sqrt(d)[:, None], k, seed=0, n_init=1, max_iter=100)
+    assert metrics.balance_multiset(lab, g.groups, k, h) == metrics.balance_multiset(oref, g.groups, k, h)
+    omine, _, _ = oracle_kmeans(H, k, seed=0, n_init=1, max_iter=100)
+    assert np.array_equal(omine, lab)
+
+
 def test_h1_plain_sc(built_lib):
     cells = cell_sizes_equal(1500, 4, 1)
     probs = category_probabilities(cells, 40, (0.7, 0.0, 0.3, 0.0))

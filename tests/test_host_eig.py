@@ -17,6 +17,8 @@ void check_cuda(cudaError_t, const char*) {}
 void fail(int, const std::string&) { throw 1; }
 }
 extern "C" void eig(int m, double* A, double* w) { sfairsc::host_symmetric_eig(m, A, w); }
+extern "C" int eig_limited(int m, double* A, double* w, int sweeps) { return sfairsc::host_symmetric_eig(m, A, w, sweeps) ? 1 : 0; }
+extern "C" int eig_jacobi(int m, double* A, double* w) { return sfairsc::host_symmetric_eig_jacobi(m, A, w) ? 1 : 0; }
 '''
 
 
@@ -31,6 +33,8 @@ def eiglib():
     subprocess.run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", *inc, SRC, drv, "-o", so], check=True)
     lib = ctypes.CDLL(so)
     lib.eig.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    lib.eig_limited.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+    lib.eig_jacobi.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
     return lib
 
 
@@ -65,3 +69,34 @@ def test_arrowhead_and_clusters(eiglib):
     eiglib.eig(m, M.ctypes.data, w.ctypes.data)
     np.testing.assert_allclose(w, np.linalg.eigvalsh(A), atol=1e-13)
     np.testing.assert_allclose(A @ M, M * w, atol=1e-12)
+
+
+def test_sweep_limit_reports_failure_and_jacobi_recovers(eiglib):
+    """A QR iteration cut off after 3 steps says so; the Jacobi fallback then gives the decomposition."""
+    m = 30
+    rng = np.random.default_rng(11)
+    A = rng.standard_normal((m, m))
+    A = A + A.T
+    M = np.asfortranarray(A.copy())
+    w = np.empty(m)
+    assert eiglib.eig_limited(m, M.ctypes.data, w.ctypes.data, 3) == 0
+    M = np.asfortranarray(A.copy())
+    assert eiglib.eig_limited(m, M.ctypes.data, w.ctypes.data, -1) == 1
+    M = np.asfortranarray(A.copy())
+    assert eiglib.eig_jacobi(m, M.ctypes.data, w.ctypes.data) == 1
+    ref = np.linalg.eigvalsh(A)
+    np.testing.assert_allclose(w, ref, atol=1e-12 * np.abs(ref).max())
+    np.testing.assert_allclose(M.T @ M, np.eye(m), atol=1e-12)
+    np.testing.assert_allclose(A @ M, M * w, atol=1e-11 * np.abs(ref).max())
+
+
+def test_nonfinite_projected_matrix_is_flagged(eiglib):
+    """A NaN never deflates: the QR iteration reports failure and Jacobi refuses the input."""
+    m = 12
+    A = np.diag(np.arange(m, dtype=float)) + np.diag(np.ones(m - 1), 1) + np.diag(np.ones(m - 1), -1)
+    A[5, 6] = A[6, 5] = np.nan
+    w = np.empty(m)
+    M = np.asfortranarray(A.copy())
+    assert eiglib.eig_limited(m, M.ctypes.data, w.ctypes.data, -1) == 0
+    M = np.asfortranarray(A.copy())
+    assert eiglib.eig_jacobi(m, M.ctypes.data, w.ctypes.data) == 0
