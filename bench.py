@@ -718,6 +718,10 @@ def run_ours(args):
         s = FairSC(rp, ci, v, gr, k=k, h=h, prec=args.prec, block=args.block)
         opx = time_operator(B, s, dev, stream, g, s_v, s_x, (1, 4), peak)
         s.close()
+        # the same without shared-memory windows (every gather from L2), for comparison
+        s = FairSC(rp, ci, v, gr, k=k, h=h, prec=args.prec, block=args.block, spmv_window=-1)
+        line["operator_no_window"] = time_operator(B, s, dev, stream, g, s_v, s_x, (1, 4), peak)
+        s.close()
         line["operator"] = opx
         # plain FP64 GPU path on the same graph, block 1 and block 4 (block 4 isolates the precision effect)
         for blk in (1, 4):

@@ -99,7 +99,15 @@ typedef struct {
                               sfairsc_solve / sfairsc_apply_operator call waits on a device flag that
                               nothing sets, so that call ends in DEVICE_TIMEOUT after wait_limit_us
                               (no fault, no hang); the hook is then cleared and later calls run normally */
-  int32_t reserved[6];
+  int32_t spmv_window;     /* 0: the operator's SpMV stages, per row segment, a slice of its input vector
+                              in shared memory where that serves enough of the segment's gathers (chosen
+                              at create from the column distribution); -1: never (every gather from L2) */
+  int32_t orth_mode;       /* reorthogonalisation of each new Krylov block.  0: classical Gram-Schmidt
+                              twice with the second projection deferred -- the block is stored after one
+                              projection and corrected during the next step's first pass over the basis
+                              (two passes over the basis per step); 1: the DGKS test of ARPACK, a third
+                              pass when a column kept less than 1/sqrt(2) of its norm */
+  int32_t reserved[4];
 } sfairsc_opts;
 
 typedef struct {
@@ -127,7 +135,10 @@ typedef struct {
   float ms_final;          /* device time of the final FP64 check, projection and embedding */
   int32_t host_eig_fallbacks; /* projected eigenproblems whose QR iteration hit its sweep limit and were
                                  solved again by cyclic Jacobi */
-  int32_t reserved[7];
+  int32_t spmv_segments;   /* row segments of the operator's SpMV at the solve's block size */
+  int32_t spmv_windowed;   /* of those, segments that stage a shared-memory window of the input */
+  float spmv_in_window;    /* fraction of the stored entries whose gather is served by a window */
+  int32_t reserved[4];
 } sfairsc_info;
 
 typedef struct sfairsc_ctx sfairsc_ctx;

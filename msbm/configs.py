@@ -17,6 +17,11 @@ Workloads (sizes as named):
   msbm_n200k_k10_h4_gauss n = 200,000, 10 clusters, 4 groups, mean degree 48,
                           Gaussian-kernel weights exp(-r^2 / (2 s^2)), s = 2,
                           16-d features, seed 4
+  paper_msbm(n, h)        the experiments' m-SBM (Exp. 1, App. C): k = 5 equal
+                          clusters, h equal groups, probabilities
+                          (a, b, c, d) = (10, 7, 4, 1) (log n / n)^(2/3) with
+                          a same cluster & same group, b other cluster & same
+                          group, c same cluster & other group, d neither
 """
 from __future__ import annotations
 
@@ -98,6 +103,18 @@ def msbm_n200k_k10_h4_gauss(scale: float = 1.0, bandwidth: float = 2.0):
     g.values = w.astype(np.float32).astype(np.float64)
     return {"name": "msbm_n200k_k10_h4_gauss", "graph": g, "k": k, "h": h, "value_dtype": "f32",
             "prec": "mixed", "r2": r2, "features": x, "bandwidth": bandwidth}
+
+
+def paper_msbm(n: int, h: int, k: int = 5, seed: int = 0):
+    """The m-SBM of the paper's experiments (App. B.2 model, Exp. 1 and App. C sizes): fair
+    ground truth (equal cells), a > b > c > d so that edges follow groups more than clusters and
+    unconstrained SC tends to split by group."""
+    cells = cell_sizes_equal(n, k, h)
+    base = (np.log(n) / n) ** (2.0 / 3.0)
+    probs = {(True, True): min(1.0, 10 * base), (False, True): min(1.0, 7 * base),
+             (True, False): min(1.0, 4 * base), (False, False): min(1.0, base)}
+    g = sample_msbm(cells, probs, seed=seed * 1000 + 7 * h + n % 997)
+    return {"name": f"paper_msbm_n{n}_h{h}", "graph": g, "k": k, "h": h, "value_dtype": "f64", "prec": "fp64"}
 
 
 BUILDERS = {

@@ -28,7 +28,8 @@ class Opts(ctypes.Structure):
         ("basis", ctypes.c_int32), ("prec", ctypes.c_int32), ("block", ctypes.c_int32),
         ("seed", ctypes.c_uint64), ("kmeans_seed", ctypes.c_uint64), ("kmeans_n_init", ctypes.c_int32),
         ("kmeans_max_iter", ctypes.c_int32), ("validate", ctypes.c_int32), ("profile", ctypes.c_int32),
-        ("wait_limit_us", ctypes.c_int32), ("fault_inject", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6),
+        ("wait_limit_us", ctypes.c_int32), ("fault_inject", ctypes.c_int32), ("spmv_window", ctypes.c_int32),
+        ("orth_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4),
     ]
 
 
@@ -42,7 +43,8 @@ class Info(ctypes.Structure):
         ("n_operator", ctypes.c_int32), ("n_orth", ctypes.c_int32), ("n_launches", ctypes.c_int32),
         ("orth_cols", ctypes.c_int32), ("basis", ctypes.c_int32), ("block", ctypes.c_int32),
         ("orth_sweeps", ctypes.c_int32), ("ms_restart", ctypes.c_float), ("ms_host_eig", ctypes.c_float),
-        ("ms_final", ctypes.c_float), ("host_eig_fallbacks", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7),
+        ("ms_final", ctypes.c_float), ("host_eig_fallbacks", ctypes.c_int32), ("spmv_segments", ctypes.c_int32),
+        ("spmv_windowed", ctypes.c_int32), ("spmv_in_window", ctypes.c_float), ("reserved", ctypes.c_int32 * 4),
     ]
 
     def as_dict(self):
@@ -252,7 +254,8 @@ def sfairsc_solve_batched(graphs, opts=None, stream=None, allow=(0,)):
 
 
 def make_opts(prec="mixed", block=1, tol=1e-6, basis=0, max_restarts=200, sigma=None, seed=1, kmeans_seed=0,
-              kmeans_n_init=1, kmeans_max_iter=100, validate=1, profile=0, wait_limit_us=0, fault_inject=0) -> Opts:
+              kmeans_n_init=1, kmeans_max_iter=100, validate=1, profile=0, wait_limit_us=0, fault_inject=0,
+              spmv_window=0, orth_mode=0) -> Opts:
     o = sfairsc_opts_default()
     o.prec = SFAIRSC_PREC_FP64 if prec == "fp64" else SFAIRSC_PREC_MIXED
     o.block = int(block)
@@ -268,4 +271,6 @@ def make_opts(prec="mixed", block=1, tol=1e-6, basis=0, max_restarts=200, sigma=
     o.profile = int(profile)
     o.wait_limit_us = int(wait_limit_us)
     o.fault_inject = int(fault_inject)
+    o.spmv_window = int(spmv_window)
+    o.orth_mode = int(orth_mode)
     return o

@@ -380,6 +380,28 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   c->op64.lanes_per_row = lanes_for(4.0);
   c->proj64 = c->op64;
   c->proj64.mode = 1;
+  // shared-memory windows of the SpMV input, one table per block size, for both precisions
+  if (c->opts.spmv_window == 0) {
+    std::vector<int32_t> rows_h(grid + 1);
+    check_cuda(cudaMemcpyAsync(rows_h.data(), c->cta_rows, sizeof(int32_t) * (grid + 1), cudaMemcpyDeviceToHost, s),
+               "d2h");
+    check_cuda(cudaStreamSynchronize(s), "row partition");
+    auto alloc = [](void* ctx, size_t bytes) -> void* { return static_cast<sfairsc_ctx*>(ctx)->dalloc<unsigned char>(bytes); };
+    const int bs[3] = {1, 2, 4};
+    for (int i = 0; i < 3; ++i) {
+      const int vs = c->vt == VecType::F64 ? 8 : 4;
+      const size_t base = operator_smem_bytes(threads, h, bs[i], c->vt);
+      c->op.win[i] = build_window_table(n, c->row_ptr, c->col, rows_h, window_rows_for(bs[i], vs, base), bs[i] * vs,
+                                        alloc, c, s);
+      if (c->vt == VecType::F64) {
+        c->op64.win[i] = c->op.win[i];
+      } else {
+        const size_t base64 = operator_smem_bytes(threads, h, bs[i], VecType::F64);
+        c->op64.win[i] = build_window_table(n, c->row_ptr, c->col, rows_h, window_rows_for(bs[i], 8, base64),
+                                            bs[i] * 8, alloc, c, s);
+      }
+    }
+  }
 
   // Krylov basis
   c->B = std::max(1, std::min(SFAIRSC_MAX_BLOCK, c->opts.block));
@@ -431,6 +453,7 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   q.brk_step = c->brk_step;
   q.sweeps = c->sweeps;
   q.wait_ns = wait_ns;
+  q.pend = c->dalloc<double>(256 * 4);
   check_cuda(cudaMallocHost((void**)&c->Hh, sizeof(double) * c->ldh * m), "pinned allocation");
   check_cuda(cudaMallocHost((void**)&c->Yh, sizeof(double) * m * m), "pinned allocation");
   check_cuda(cudaMallocHost(&c->Ystage, sizeof(double) * m * m), "pinned allocation");
@@ -486,7 +509,7 @@ void apply_op(sfairsc_ctx* c, bool fp64, const void* w, int64_t wrs, int64_t wcs
   }
 }
 
-void orth(sfairsc_ctx* c, int J, int j) {
+void orth(sfairsc_ctx* c, int J, int j, bool pend_in = false, bool defer = false) {
   const bool timed = c->opts.profile != 0;
   cudaEvent_t a = nullptr, b = nullptr;
   if (timed) {
@@ -494,7 +517,7 @@ void orth(sfairsc_ctx* c, int J, int j) {
     b = c->take_event();
     check_cuda(cudaEventRecord(a, c->stream), "event record");
   }
-  launch_orth(c->orth, c->vt, J, j, c->B, c->stream);
+  launch_orth(c->orth, c->vt, J, j, c->B, pend_in, defer, c->stream);
   c->n_launches += 1;
   if (timed) {
     check_cuda(cudaEventRecord(b, c->stream), "event record");
@@ -636,9 +659,12 @@ int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* label
   const double tol = c->opts.tol * c->sigma;
   for (;;) {
     check_cuda(cudaMemcpyAsync(c->brk_step, &kNoBreak, sizeof(int), cudaMemcpyHostToDevice, s), "h2d");
+    // deferred second projection (opts.orth_mode 0): each step's new block is stored before its
+    // second projection; the next step applies it in its first sweep, the restart to the carried block
+    const bool defer = c->opts.orth_mode == 0;
     for (int j = j0; j < m; j += B) {
       apply_op(c, false, c->Q, 4, 1, c->U, 4, 1, B);  // Q holds V[:, j:j+B]
-      orth(c, j + B, j);
+      orth(c, j + B, j, defer && j > j0, defer);
       orth_cols += j + B;
       matvecs += B;
       ++n_op;
@@ -715,7 +741,8 @@ int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* label
         eb = c->take_event();
         check_cuda(cudaEventRecord(ea, s), "event record");
       }
-      launch_restart(c->vt, n, c->V, c->ldv, mv, K, B, c->Yd, c->Q, s);
+      launch_restart(c->vt, n, c->V, c->ldv, mv, K, B, c->Yd, c->Q,
+                     (c->opts.orth_mode == 0 && !broke) ? c->orth.pend : nullptr, s);
       if (c->opts.profile) {
         check_cuda(cudaEventRecord(eb, s), "event record");
         c->ev_restart.emplace_back(ea, eb);
@@ -773,6 +800,12 @@ int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* label
   inf.ms_host_eig = (float)ms_eig;
   inf.n_operator = n_op;
   inf.host_eig_fallbacks = eig_fallbacks;
+  {
+    const WindowTable& wt = c->op.win[B == 1 ? 0 : B == 2 ? 1 : 2];
+    inf.spmv_segments = wt.nseg;
+    inf.spmv_windowed = wt.windowed;
+    inf.spmv_in_window = c->nnz > 0 ? (float)((double)wt.in_window / (double)c->nnz) : 0.f;
+  }
   inf.n_orth = n_orth;
   inf.orth_cols = orth_cols;
   {
@@ -914,7 +947,8 @@ int sfairsc_create(sfairsc_ctx** out, int64_t n, int64_t nnz, const int32_t* row
   if (opts) c->opts = *opts;
   if (!(c->opts.tol > 0.0) || c->opts.max_restarts < 0 || c->opts.block < 1 || c->opts.block > SFAIRSC_MAX_BLOCK ||
       c->opts.kmeans_n_init < 1 || c->opts.kmeans_max_iter < 1 || (c->opts.prec != 0 && c->opts.prec != 1) ||
-      c->opts.wait_limit_us < 0 || (c->opts.fault_inject != 0 && c->opts.fault_inject != 1)) {
+      c->opts.wait_limit_us < 0 || (c->opts.fault_inject != 0 && c->opts.fault_inject != 1) ||
+      (c->opts.spmv_window != 0 && c->opts.spmv_window != -1) || (c->opts.orth_mode != 0 && c->opts.orth_mode != 1)) {
     g_last_error = "invalid options";
     return SFAIRSC_ERR_INVALID_ARG;
   }

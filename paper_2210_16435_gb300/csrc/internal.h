@@ -42,6 +42,20 @@ struct SfError {
 // Record the detail message returned by sfairsc_last_error() on this thread.
 void set_last_error(const std::string& msg);
 
+// Shared-memory windows of the SpMV input (one table per block size b): each
+// CTA's rows are cut into segments; a segment with ws >= 0 stages rows
+// [ws, ws + win_rows) of ytil (b values each) in shared memory and gathers
+// from there the entries whose column falls inside, and from L2 the others.
+struct WindowTable {
+  int win_rows = 0;                // rows per window (0: no windows)
+  const int32_t* seg_row = nullptr;  // int32[nseg + 1]: first row of each segment
+  const int32_t* seg_ws = nullptr;   // int32[nseg]: window start row, or -1 (no window)
+  const int32_t* cta_seg = nullptr;  // int32[grid + 1]: first segment of each CTA
+  int nseg = 0;
+  int windowed = 0;                // segments with a window
+  long long in_window = 0;         // stored entries whose column falls in their segment's window
+};
+
 // Operator launch description (everything the fused kernel needs).
 struct OpPlan {
   int n = 0;
@@ -68,7 +82,17 @@ struct OpPlan {
   unsigned* work = nullptr;    // 1 word: dynamic row-block counter of the SpMV
   unsigned long long wait_ns = 2000000000ull;  // bound of every device-side wait
   const unsigned* stall_flag = nullptr;  // non-null: the launch first waits for this word (never set) to become nonzero
+  WindowTable win[3];  // by block size b = 1, 2, 4 (index 0, 1, 2)
 };
+
+// Rows of ytil (b values of vs bytes) a window may hold next to the kernel's other shared memory.
+int window_rows_for(int b, int vs, size_t base_smem);
+// Choose the windows of the CTA row ranges cta_rows (host copy, grid + 1 entries) for windows of
+// win_rows rows: a device pass histograms each 256-row chunk's columns, the host merges chunks
+// into segments.  Allocations go through alloc (device memory owned by the caller).
+WindowTable build_window_table(int n, const int32_t* row_ptr, const int32_t* col, const std::vector<int32_t>& cta_rows,
+                               int win_rows, int bytes_per_row, void* (*alloc)(void*, size_t), void* alloc_ctx,
+                               cudaStream_t s);
 
 // Launch out = L_n^sigma w for nvec vectors; element (r, v) of w is w[r*wrs + v*wcs]
 // and of out is out[r*ors + v*ocs].
@@ -109,17 +133,22 @@ struct OrthPlan {
   int* brk_step = nullptr;    // smallest step j whose new block lost rank (atomicMin)
   int* sweeps = nullptr;      // accumulates the number of passes over V
   unsigned long long wait_ns = 2000000000ull;  // bound of every device-side wait
+  double* pend = nullptr;     // 256 x 4: pending second-projection correction of the newest block
 };
 // Orthogonalise the B columns in U against V[:, 0:J] (CGS2), record the
 // coefficients in H[0:J, j:j+B], orthonormalise the block (CholQR), store it
 // as V[:, J:J+B] and its R factor in H[J:J+B, j:j+B].
-void launch_orth(const OrthPlan& p, VecType vt, int J, int j, int B, cudaStream_t s);
+// pend_in: V[:, j:j+B] still owes its second projection (correction p.pend, j x B), applied in the
+// first sweep.  defer: leave the new block's second projection pending (p.pend, J x B) instead of
+// a third sweep; the next launch, or the restart, applies it.
+void launch_orth(const OrthPlan& p, VecType vt, int J, int j, int B, bool pend_in, bool defer, cudaStream_t s);
 int orth_max_grid(VecType vt, int B, int threads);
-// V[:, 0:K] = V[:, 0:m] Y (Y: m x K row-major on device, in the basis precision), then V[:, K:K+B] = V[:, m:m+B].
-// V is stored as ldv/4 panels of n x 4 (panel p = columns 4p..4p+3).
+// V[:, 0:K] = V[:, 0:m] Y (Y: m x K row-major on device, in the basis precision), then V[:, K:K+B] =
+// V[:, m:m+B] - V[:, 0:m] E when E (m x B row-major FP64, the carried block's pending correction) is
+// given, else V[:, m:m+B].  V is stored as ldv/4 panels of n x 4 (panel p = columns 4p..4p+3).
 // Q (n x 4 row-major) receives the carried block too.
 void launch_restart(VecType vt, int n, void* V, int64_t ldv, int m, int K, int B, const void* Y, void* Q,
-                    cudaStream_t s);
+                    const double* E, cudaStream_t s);
 // Fill V[:, 0:B] with a seeded pseudo-random block.
 void launch_random_block(VecType vt, int n, void* V, int64_t ldv, int B, uint64_t seed, cudaStream_t s);
 // X64 = V[:, 0:m] Y (Y: m x k row-major, in the basis precision), X64 n x k column-major FP64; V unchanged.

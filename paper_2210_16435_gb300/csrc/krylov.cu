@@ -38,7 +38,8 @@ __device__ __forceinline__ void lds4(const VT* p, VT (&x)[4]) {
 // mode 1: into X (column-major n x K, FP64).
 template <typename VT, int MODE>
 __global__ void __launch_bounds__(256) tile_gemm_kernel(int n, VT* V, int64_t ldv, int m, int K, int B,
-                                                        const VT* __restrict__ Y, VT* Q, double* X) {
+                                                        const VT* __restrict__ Y, VT* Q, double* X,
+                                                        const double* __restrict__ E) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int width = m + B;
   VT* Vt = reinterpret_cast<VT*>(sm);  // width x kTS (transposed tile)
@@ -161,7 +162,12 @@ __global__ void __launch_bounds__(256) tile_gemm_kernel(int n, VT* V, int64_t ld
     __syncthreads();
     for (int i = t; i < rows * B; i += blockDim.x) {
       const int rr = i / B, v = i % B;
-      const VT x = Vt[(size_t)(m + v) * kTS + rr];
+      VT x = Vt[(size_t)(m + v) * kTS + rr];
+      if (E) {  // the carried block's pending second projection: x -= V[r, 0:m] E[:, v]
+        VT d = VT(0);
+        for (int c = 0; c < m; ++c) d = fma(Vt[(size_t)c * kTS + rr], (VT)E[c * B + v], d);
+        x -= d;
+      }
       V[((K + v) >> 2) * pn + (size_t)(rbase + rr) * 4 + ((K + v) & 3)] = x;
       Q[(size_t)(rbase + rr) * 4 + v] = x;
     }
@@ -170,28 +176,29 @@ __global__ void __launch_bounds__(256) tile_gemm_kernel(int n, VT* V, int64_t ld
 
 template <typename VT, int MODE>
 static void tile_gemm_launch(int n, VT* V, int64_t ldv, int m, int K, int B, const VT* Y, VT* Q, double* X,
-                             cudaStream_t s) {
+                             const double* E, cudaStream_t s) {
   size_t smem = sizeof(VT) * ((size_t)(m + B) * kTS + (size_t)m * 64);
   if (MODE == 1)  // the Y chunk's space also holds the 64 x (kTR + 1) FP64 output tile
     smem = std::max(smem, sizeof(VT) * (size_t)(m + B) * kTS + sizeof(double) * 64 * (kTR + 1));
   if (smem > 227 * 1024) fail(SFAIRSC_ERR_UNSUPPORTED, "Krylov basis too wide for the restart tile in this precision");
   auto kern = tile_gemm_kernel<VT, MODE>;
   check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "tile gemm smem");
-  kern<<<(n + kTR - 1) / kTR, 256, smem, s>>>(n, V, ldv, m, K, B, Y, Q, X);
+  kern<<<(n + kTR - 1) / kTR, 256, smem, s>>>(n, V, ldv, m, K, B, Y, Q, X, E);
   check_cuda(cudaGetLastError(), "tile gemm launch");
 }
 
 void launch_restart(VecType vt, int n, void* V, int64_t ldv, int m, int K, int B, const void* Y, void* Q,
-                    cudaStream_t s) {
+                    const double* E, cudaStream_t s) {
   if (vt == VecType::F64)
-    tile_gemm_launch<double, 0>(n, (double*)V, ldv, m, K, B, (const double*)Y, (double*)Q, nullptr, s);
-  else tile_gemm_launch<float, 0>(n, (float*)V, ldv, m, K, B, (const float*)Y, (float*)Q, nullptr, s);
+    tile_gemm_launch<double, 0>(n, (double*)V, ldv, m, K, B, (const double*)Y, (double*)Q, nullptr, E, s);
+  else tile_gemm_launch<float, 0>(n, (float*)V, ldv, m, K, B, (const float*)Y, (float*)Q, nullptr, E, s);
 }
 
 void launch_ritz(VecType vt, int n, const void* V, int64_t ldv, int m, int k, const void* Y, double* X64,
                  cudaStream_t s) {
-  if (vt == VecType::F64) tile_gemm_launch<double, 1>(n, (double*)V, ldv, m, k, 0, (const double*)Y, nullptr, X64, s);
-  else tile_gemm_launch<float, 1>(n, (float*)V, ldv, m, k, 0, (const float*)Y, nullptr, X64, s);
+  if (vt == VecType::F64)
+    tile_gemm_launch<double, 1>(n, (double*)V, ldv, m, k, 0, (const double*)Y, nullptr, X64, nullptr, s);
+  else tile_gemm_launch<float, 1>(n, (float*)V, ldv, m, k, 0, (const float*)Y, nullptr, X64, nullptr, s);
 }
 
 __global__ void column_resid_kernel(int n, int k, const double* __restrict__ X, const double* __restrict__ AX,

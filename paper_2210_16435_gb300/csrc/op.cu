@@ -46,6 +46,12 @@ struct OpArgs {
   unsigned* work;  // dynamic row-block counter of the SpMV phase
   unsigned long long wait_ns;  // bound of every grid-barrier wait
   const unsigned* stall;       // fault-injection hook: wait for this (never set) word first
+  // shared-memory windows of ytil (WindowTable for this block size); seg_row == nullptr: none
+  const int32_t* __restrict__ seg_row;
+  const int32_t* __restrict__ seg_ws;
+  const int32_t* __restrict__ cta_seg;
+  int win_rows;
+  int win_off;  // byte offset of the window in dynamic shared memory
 };
 
 template <typename VT, int B>
@@ -332,32 +338,26 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
       a.ytil[(size_t)r * B + v] = a.normalized ? sc * y : y;
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) *a.work = 0u;  // no CTA takes a block before the barrier
   if (!grid_sync(a.bar, a.err, a.wait_ns)) return;
 
-  // ---------------- phase C: t = L_n y, written to out
-  // Warps take blocks of 4 row groups from a global counter (load balance
-  // across CTAs); Lr lanes per row, each holding up to U (column, weight)
-  // pairs of its row per pass; within a block the pairs of the next row group
-  // and the bounds of the group after it are loaded while this group's ytil
-  // rows are gathered.  Sums per row by a fixed shuffle tree (reproducible).
+  // ---------------- phase C: t = L_n y over this CTA's rows, written to out
+  // The CTA's rows come as segments; a segment with a window first stages
+  // ytil rows [ws, ws + win_rows) in shared memory, and each gather reads
+  // from there when its column falls inside, from L2 otherwise (one generic
+  // load either way).  A warp takes row groups of 32 / Lr rows in turn; Lr
+  // lanes per row each hold up to U (column, weight) pairs of the row per
+  // pass, and the next group's pairs are loaded while this group's ytil rows
+  // are gathered.  Sums per row by a fixed shuffle tree (reproducible).
   {
     constexpr int U = sizeof(VT) == 4 ? 8 : 4;
-    constexpr int kGroupsPerBlock = 4;
     const int Lr = a.lanes;
     const int sub = lane & (Lr - 1);
     const int rpw = 32 / Lr;
     const int n = a.n;
-    auto bounds = [&](int rb, int rend, int& e, int& e1) {
-      const int r = rb + lane / Lr;
-      if (r < rend) {
-        e = __ldg(a.row_ptr + r) + sub;
-        e1 = __ldg(a.row_ptr + r + 1);
-      } else {
-        e = 0;
-        e1 = 0;
-      }
-    };
+    const int warp = threadIdx.x >> 5;
+    VT* win = reinterpret_cast<VT*>(smem_raw + a.win_off);
+    const int sg0 = a.seg_row ? a.cta_seg[blockIdx.x] : 0;
+    const int sg1 = a.seg_row ? a.cta_seg[blockIdx.x + 1] : 1;
     auto fetch = [&](int e, int e1, int (&c)[U], VT (&wv)[U]) {
 #pragma unroll
       for (int u = 0; u < U; ++u) {
@@ -367,94 +367,100 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
         wv[u] = in ? val_as<VT>(a.val[ee]) : VT(0);
       }
     };
-    const int blk_rows = rpw * kGroupsPerBlock;
-    const int nblocks = (n + blk_rows - 1) / blk_rows;
-    auto grab = [&]() {
-      int b = 0;
-      if (lane == 0) b = (int)atomicAdd(a.work, 1u);
-      return __shfl_sync(0xffffffffu, b, 0);
-    };
-    // look-ahead iterator over the row groups of the blocks this warp takes
-    // (row base n = exhausted); the block after the current one is taken early
-    int la_blk = grab(), la_next = grab();
-    int la_rb = la_blk < nblocks ? la_blk * blk_rows : n;
-    auto advance = [&]() {
-      if (la_rb >= n) return;
-      la_rb += rpw;
-      if (la_rb >= min(n, la_blk * blk_rows + blk_rows)) {
-        la_blk = la_next;
-        la_rb = la_blk < nblocks ? la_blk * blk_rows : n;
-        if (la_blk < nblocks) la_next = grab();
+    for (int sg = sg0; sg < sg1; ++sg) {
+      const int rs = a.seg_row ? a.seg_row[sg] : r0;
+      const int re = a.seg_row ? a.seg_row[sg + 1] : r1;
+      const int ws = a.seg_row ? a.seg_ws[sg] : -1;
+      int wlen = 0;
+      if (ws >= 0) {
+        wlen = min(a.win_rows, n - ws);
+        __syncthreads();  // the previous segment's gathers are done with the window
+        // ws is a multiple of 4 rows, so the copy starts 16-byte aligned for every b
+        const int total = wlen * B;  // VT elements
+        constexpr int PER = 16 / (int)sizeof(VT);
+        const int nv = total / PER;
+        const int4* src = reinterpret_cast<const int4*>(a.ytil + (size_t)ws * B);
+        int4* dst = reinterpret_cast<int4*>(win);
+        for (int i = threadIdx.x; i < nv; i += blockDim.x) dst[i] = __ldcg(src + i);
+        for (int i = nv * PER + threadIdx.x; i < total; i += blockDim.x) win[i] = __ldcg(a.ytil + (size_t)ws * B + i);
+        __syncthreads();
       }
-    };
-    auto rend_of = [&](int rb) { return min(n, (rb / blk_rows) * blk_rows + blk_rows); };
-    int rb_cur = la_rb;
-    advance();
-    int rb_nx = la_rb;
-    advance();
-    int e_cur, e1_cur, e_nx, e1_nx;
-    int c_cur[U];
-    VT w_cur[U];
-    bounds(rb_cur, rb_cur < n ? rend_of(rb_cur) : n, e_cur, e1_cur);
-    fetch(e_cur, e1_cur, c_cur, w_cur);
-    bounds(rb_nx, rb_nx < n ? rend_of(rb_nx) : n, e_nx, e1_nx);
-    while (rb_cur < n) {
-      int c_nx[U];
-      VT w_nx[U];
-      fetch(e_nx, e1_nx, c_nx, w_nx);  // the next group's pairs, in flight during this group's gathers
-      const int rb_nn = la_rb;
-      advance();
-      int e_nn, e1_nn;
-      bounds(rb_nn, rb_nn < n ? rend_of(rb_nn) : n, e_nn, e1_nn);
-      const int rend = rend_of(rb_cur);
-      VT sacc[B];
+      const unsigned wsu = (unsigned)ws, wlenu = (unsigned)wlen;
+      const int ngroups = (re - rs + rpw - 1) / rpw;
+      auto bounds = [&](int q, int& e, int& e1) {
+        const int r = rs + q * rpw + lane / Lr;
+        if (q < ngroups && r < re) {
+          e = __ldg(a.row_ptr + r) + sub;
+          e1 = __ldg(a.row_ptr + r + 1);
+        } else {
+          e = 0;
+          e1 = 0;
+        }
+      };
+      int q = warp;
+      int e_cur, e1_cur, e_nx, e1_nx;
+      int c_cur[U];
+      VT w_cur[U];
+      bounds(q, e_cur, e1_cur);
+      fetch(e_cur, e1_cur, c_cur, w_cur);
+      bounds(q + nwarps, e_nx, e1_nx);
+      for (; q < ngroups; q += nwarps) {
+        int c_nx[U];
+        VT w_nx[U];
+        fetch(e_nx, e1_nx, c_nx, w_nx);  // the next group's pairs, in flight during this group's gathers
+        int e_nn, e1_nn;
+        bounds(q + 2 * nwarps, e_nn, e1_nn);
+        VT sacc[B];
 #pragma unroll
-      for (int v = 0; v < B; ++v) sacc[v] = VT(0);
+        for (int v = 0; v < B; ++v) sacc[v] = VT(0);
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (c_cur[u] >= 0) {
+        for (int u = 0; u < U; ++u) {
+          if (c_cur[u] >= 0) {
+            const unsigned off = (unsigned)c_cur[u] - wsu;
+            const VT* src = off < wlenu ? win + (size_t)off * B : a.ytil + (size_t)c_cur[u] * B;
+            VT y[B];
+            load_row<VT, B>(src, y);
+#pragma unroll
+            for (int v = 0; v < B; ++v) sacc[v] = fma(w_cur[u], y[v], sacc[v]);
+          }
+        }
+        for (int e = e_cur + U * Lr; e < e1_cur; e += Lr) {  // rows longer than U * Lr entries
+          const int c = __ldg(a.col + e);
+          const VT w = val_as<VT>(a.val[e]);
+          const unsigned off = (unsigned)c - wsu;
+          const VT* src = off < wlenu ? win + (size_t)off * B : a.ytil + (size_t)c * B;
           VT y[B];
-          load_row<VT, B>(a.ytil + (size_t)c_cur[u] * B, y);
+          load_row<VT, B>(src, y);
 #pragma unroll
-          for (int v = 0; v < B; ++v) sacc[v] = fma(w_cur[u], y[v], sacc[v]);
+          for (int v = 0; v < B; ++v) sacc[v] = fma(w, y[v], sacc[v]);
         }
-      }
-      for (int e = e_cur + U * Lr; e < e1_cur; e += Lr) {  // rows longer than U * Lr entries
-        const int c = __ldg(a.col + e);
-        const VT w = val_as<VT>(a.val[e]);
-        VT y[B];
-        load_row<VT, B>(a.ytil + (size_t)c * B, y);
+        for (int o = Lr >> 1; o > 0; o >>= 1)
 #pragma unroll
-        for (int v = 0; v < B; ++v) sacc[v] = fma(w, y[v], sacc[v]);
-      }
-      for (int o = Lr >> 1; o > 0; o >>= 1)
+          for (int v = 0; v < B; ++v) sacc[v] += __shfl_xor_sync(0xffffffffu, sacc[v], o);
+        const int r = rs + q * rpw + lane / Lr;
+        if (r < re && sub == 0) {
+          const int g = a.lab[r];
+          const VT sc = scale(r);
+          VT dd = VT(1);
+          if (!a.normalized) dd = (VT)a.deg[r];
+          VT wr[B];
+          load_strided<VT, B>(a.w, r, a.wrs, a.wcs, wr);
 #pragma unroll
-        for (int v = 0; v < B; ++v) sacc[v] += __shfl_xor_sync(0xffffffffu, sacc[v], o);
-      const int r = rb_cur + lane / Lr;
-      if (r < rend && sub == 0) {
-        const int g = a.lab[r];
-        const VT sc = scale(r);
-        VT dd = VT(1);
-        if (!a.normalized) dd = (VT)a.deg[r];
-        VT wr[B];
-        load_strided<VT, B>(a.w, r, a.wrs, a.wcs, wr);
-#pragma unroll
-        for (int v = 0; v < B; ++v) {
-          const VT y = wr[v] - sc * coefAv[g * B + v];
-          a.out[r * a.ors + v * a.ocs] = a.normalized ? y - sc * sacc[v] : dd * y - sacc[v];
+          for (int v = 0; v < B; ++v) {
+            const VT y = wr[v] - sc * coefAv[g * B + v];
+            a.out[r * a.ors + v * a.ocs] = a.normalized ? y - sc * sacc[v] : dd * y - sacc[v];
+          }
         }
-      }
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        c_cur[u] = c_nx[u];
-        w_cur[u] = w_nx[u];
+        for (int u = 0; u < U; ++u) {
+          c_cur[u] = c_nx[u];
+          w_cur[u] = w_nx[u];
+        }
+        e_cur = e_nx;
+        e1_cur = e1_nx;
+        e_nx = e_nn;
+        e1_nx = e1_nn;
       }
-      e_cur = e_nx;
-      e1_cur = e1_nx;
-      e_nx = e_nn;
-      e1_nx = e1_nn;
-      rb_cur = rb_nx;
-      rb_nx = rb_nn;
     }
   }
   if (!grouped) return;
@@ -546,7 +552,15 @@ static void launch_t(const OpPlan& p, const void* w, int64_t wrs, int64_t wcs, v
   a.work = p.work;
   a.wait_ns = p.wait_ns;
   a.stall = p.stall_flag;
-  const size_t smem = operator_smem_bytes(p.threads, p.h, B, sizeof(VT) == 8 ? VecType::F64 : VecType::F32);
+  const size_t base = operator_smem_bytes(p.threads, p.h, B, sizeof(VT) == 8 ? VecType::F64 : VecType::F32);
+  const WindowTable& wt = p.win[B == 1 ? 0 : B == 2 ? 1 : 2];
+  const bool windows = p.mode == 0 && wt.seg_row != nullptr && wt.win_rows > 0;
+  a.seg_row = windows ? wt.seg_row : nullptr;
+  a.seg_ws = windows ? wt.seg_ws : nullptr;
+  a.cta_seg = windows ? wt.cta_seg : nullptr;
+  a.win_rows = windows ? wt.win_rows : 0;
+  a.win_off = (int)((base + 15) / 16 * 16);
+  const size_t smem = (size_t)a.win_off + (windows ? (size_t)wt.win_rows * B * sizeof(VT) : 0);
   auto kern = fused_operator_kernel<VT, MT, B>;
   check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "operator smem attr");
   void* args[] = {&a};

@@ -250,6 +250,12 @@ struct OrthArgs {
   int* sweeps;
   int J, j;
   unsigned long long wait_ns;  // bound of every grid-barrier wait
+  // deferred second projection: pend_in (j x B, nullable) is the pending correction of the
+  // input block V[:, j:j+B] against V[:, 0:j]; with defer the new block is stored without its
+  // second projection, whose correction (J x B) goes to pend_out
+  const double* pend_in;
+  double* pend_out;
+  int defer;
 };
 
 // Sweep slices: SR consecutive rows of every panel V[:, 4p:4p+4] (p < np)
@@ -331,8 +337,13 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
   //     the new coefficients V^T u.
   auto sweep = [&](int kind) -> bool {
     const bool upd = kind >= 1, want_c = kind <= 1;
+    // kind 0 with a pending correction first finishes the input block: V[:, j:j+B] -= V[:, 0:j] e
+    const bool fix = kind == 0 && a.pend_in != nullptr;
+    const int Jd = upd ? J : (fix ? a.j : 0);  // columns of the row update V[:, 0:Jd] c
     if (upd)
       for (int i = threadIdx.x; i < P; i += blockDim.x) cfs[i] = (VT)__ldcg(a.coef + i);
+    else if (fix)
+      for (int i = threadIdx.x; i < a.j * B; i += blockDim.x) cfs[i] = (VT)__ldcg(a.pend_in + i);
     __syncthreads();  // coefficients in place; the slice buffers are free
     constexpr int CH = (int)sizeof(VT) / 4;
     const SliceShape sh = slice_shape<VT>(np);
@@ -388,8 +399,8 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
         VT d[B];
 #pragma unroll
         for (int v = 0; v < B; ++v) d[v] = VT(0);
-        if (upd) {
-          const int nfull = J >> 2;  // panels whose 4 columns are all < J
+        if (Jd > 0) {
+          const int nfull = Jd >> 2;  // panels whose 4 columns are all < Jd
           VT d1[B];  // a second set of chains: two panels' loads in flight per step
 #pragma unroll
           for (int v = 0; v < B; ++v) d1[v] = VT(0);
@@ -417,7 +428,7 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
           if (nfull < np && (nfull & (LPA - 1)) == g) {
             VT x[4];
             ld4(at(i, nfull), x);
-            for (int jj = 0; jj < (J & 3); ++jj)
+            for (int jj = 0; jj < (Jd & 3); ++jj)
 #pragma unroll
               for (int v = 0; v < B; ++v) d1[v] = fma(x[jj], cfs[(4 * nfull + jj) * B + v], d1[v]);
           }
@@ -428,6 +439,18 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
             for (int v = 0; v < B; ++v) d[v] += __shfl_xor_sync(0xffffffffu, d[v], o);
         }
         if (g == 0 && i < rows) {
+          if (fix) {  // the input block's row, corrected in the slice (for phase B) and in V
+            const int pt = a.j >> 2, c0 = a.j & 3;
+            VT x[4];
+            ld4(at(i, pt), x);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+              for (int v = 0; v < B; ++v)
+                if (q == c0 + v) x[q] -= d[v];
+            st4(const_cast<VT*>(at(i, pt)), x);
+            st4(a.V + (size_t)pt * pn + (size_t)(rb + i) * 4, x);
+          }
           VT u[4];
           ld4(at(i, np), u);
           if (upd) {
@@ -641,15 +664,34 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
     __syncthreads();
   };
 
+  // Entry (r, c), c < j, of the projected matrix V[:, 0:J]^T A V[:, 0:j]: the upper triangle holds
+  // the square part (symmetric), rows of the input block hold its R block and restart couplings.
+  auto hfull = [&](int r, int c) -> double {
+    return r <= c ? a.H[(size_t)r + (size_t)a.ldh * c]
+                  : (r < a.j ? a.H[(size_t)c + (size_t)a.ldh * r] : a.H[(size_t)r + (size_t)a.ldh * c]);
+  };
+  const bool defer = a.defer != 0 && J > 0;
   int sweeps = 0;
   if (J > 0) {
-    // sweep 1: c1 = V^T U and the input norms
+    // sweep 1: (finish the input block;) c1 = V^T U and the input norms
     if (!sweep(0)) return;
     ++sweeps;
     if (!grid_sync(a.bar, a.err, a.wait_ns)) return;
     reduce_owned(a.partial, kStride, gridDim.x, P, a.coef, scratch);
+    // The operator saw the input block before its correction: A q = A q_stored - A V[:, 0:j] e, and
+    // V^T A V[:, 0:j] e = H[0:J, 0:j] e, so the recorded coefficients drop that term.  (The
+    // projected vector itself is unchanged: U - V c1 removes everything in span(V) either way.)
     if (a.j >= 0)
-      for (int p = blockIdx.x; p < P; p += gridDim.x) a.H[(size_t)(p / B) + (size_t)a.ldh * (a.j + p % B)] = a.coef[p];
+      for (int p = blockIdx.x; p < P; p += gridDim.x) {
+        double hv = a.coef[p];
+        if (a.pend_in) {
+          const int r = p / B, v = p % B;
+          double t = 0.0;
+          for (int c = 0; c < a.j; ++c) t = fma(hfull(r, c), a.pend_in[c * B + v], t);
+          hv -= t;
+        }
+        a.H[(size_t)(p / B) + (size_t)a.ldh * (a.j + p % B)] = hv;
+      }
     reduce_all(a.partial, kStride, gridDim.x, kNormOff, B, unorm, scratch);
     if (!grid_sync(a.bar, a.err, a.wait_ns)) return;
     // sweep 2: U -= V c1; c2 = V^T U; Gram
@@ -663,7 +705,23 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
         if (gram_s[v * B + v] < 0.5 * unorm[v]) again = 1;  // DGKS: kept less than 1/sqrt(2) of the norm
     }
     __syncthreads();
-    if (again) {
+    if (defer) {
+      // the second projection U -= V c2 is left to the next launch: its coefficients join H, and
+      // the Gram matrix of the projected block is G - c2^T c2 (V^T V = I, V^T U = c2)
+      reduce_owned(a.partial, kStride, gridDim.x, P, a.coef, scratch);
+      if (a.j >= 0)
+        for (int p = blockIdx.x; p < P; p += gridDim.x) a.H[(size_t)(p / B) + (size_t)a.ldh * (a.j + p % B)] += a.coef[p];
+      if (!grid_sync(a.bar, a.err, a.wait_ns)) return;
+      if ((int)threadIdx.x < B * B) {
+        const int v = threadIdx.x / B, w2 = threadIdx.x % B;
+        double t = 0.0;
+        for (int c = 0; c < J; ++c) t = fma(__ldcg(a.coef + c * B + v), __ldcg(a.coef + c * B + w2), t);
+        scratch[threadIdx.x] = t;
+      }
+      __syncthreads();
+      if ((int)threadIdx.x < B * B) gram_s[threadIdx.x] -= scratch[threadIdx.x];
+      __syncthreads();
+    } else if (again) {
       reduce_owned(a.partial, kStride, gridDim.x, P, a.coef, scratch);
       if (a.j >= 0)
         for (int p = blockIdx.x; p < P; p += gridDim.x) a.H[(size_t)(p / B) + (size_t)a.ldh * (a.j + p % B)] += a.coef[p];
@@ -682,14 +740,51 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
   }
   cholesky(R1, Rd1);
 
+  // deferred mode: e1 = c2 R1^{-1} (J x B) in scratch, the pending correction after the first QR
+  auto pending_times_rinv = [&](const double* Rd, bool from_coef) {
+    if ((int)threadIdx.x < J) {
+      const int c = threadIdx.x;
+      double x[4];
+#pragma unroll
+      for (int v = 0; v < B; ++v) x[v] = from_coef ? __ldcg(a.coef + c * B + v) : scratch[c * B + v];
+      // row c of x R^{-1}: forward substitution with the upper factor
+#pragma unroll
+      for (int v = 0; v < B; ++v) {
+        double t = x[v];
+#pragma unroll
+        for (int q = 0; q < v; ++q) t -= x[q] * Rd[q * B + v];
+        x[v] = t / Rd[v * B + v];
+      }
+#pragma unroll
+      for (int v = 0; v < B; ++v) scratch[c * B + v] = x[v];
+    }
+    __syncthreads();
+  };
+  if (defer) pending_times_rinv(Rd1, true);
   if (B > 1) {
     // Cholesky QR a second time: U <- U R1^{-1}, Gram again
+    double e1tv = 0.0;  // thread v * B + w: (e1^T e1)_vw
+    if (defer) {
+      if ((int)threadIdx.x < B * B) {
+        const int v = threadIdx.x / B, w2 = threadIdx.x % B;
+        for (int c = 0; c < J; ++c) e1tv = fma(scratch[c * B + v], scratch[c * B + w2], e1tv);
+      }
+      // keep e1 while gram_rows and reduce_all reuse scratch: in this CTA's own partial row, whose
+      // coefficient slots are free once every CTA has reduced c2 (a grid barrier ago)
+      for (int i = threadIdx.x; i < J * B; i += blockDim.x) a.partial[(size_t)blockIdx.x * kStride + i] = scratch[i];
+      __syncthreads();
+    }
     gram_rows(kGram2Off, true);
     if (!grid_sync(a.bar, a.err, a.wait_ns)) return;
     reduce_all(a.partial, kStride, gridDim.x, kGram2Off, B * B, gram_s, scratch);
+    if (defer) {
+      if ((int)threadIdx.x < B * B) gram_s[threadIdx.x] -= e1tv;
+      for (int i = threadIdx.x; i < J * B; i += blockDim.x) scratch[i] = a.partial[(size_t)blockIdx.x * kStride + i];
+    }
     if (threadIdx.x < B) unorm[threadIdx.x] = 0.0;
     __syncthreads();
     cholesky(R2, Rd2);
+    if (defer) pending_times_rinv(Rd2, false);
   } else {
     if (threadIdx.x == 0) {
       R2[0] = 1.0;
@@ -736,6 +831,8 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
     }
   };
   final_rows(r0, r1);
+  if (defer && blockIdx.x == 0)
+    for (int i = threadIdx.x; i < J * B; i += blockDim.x) a.pend_out[i] = scratch[i];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (brk) {
       atomicOr(a.err, kErrBreakdown);
@@ -758,7 +855,7 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
 }
 
 template <typename VT, int B, int NC>
-static void orth_launch_t(const OrthPlan& p, int J, int j, cudaStream_t s) {
+static void orth_launch_t(const OrthPlan& p, int J, int j, bool pend_in, bool defer, cudaStream_t s) {
   OrthArgs<VT> a;
   a.n = p.n;
   a.V = static_cast<VT*>(p.V);
@@ -776,6 +873,9 @@ static void orth_launch_t(const OrthPlan& p, int J, int j, cudaStream_t s) {
   a.J = J;
   a.j = j;
   a.wait_ns = p.wait_ns;
+  a.pend_in = pend_in ? p.pend : nullptr;
+  a.pend_out = defer ? p.pend : nullptr;
+  a.defer = defer ? 1 : 0;
   const size_t smem = orth_smem_bytes<VT, NC>();
   auto kern = orth_kernel<VT, B, NC>;
   check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "orth smem attr");
@@ -784,22 +884,23 @@ static void orth_launch_t(const OrthPlan& p, int J, int j, cudaStream_t s) {
 }
 
 template <typename VT, int B>
-static void orth_launch_b(const OrthPlan& p, int J, int j, cudaStream_t s) {
-  if (J <= 128) orth_launch_t<VT, B, 1>(p, J, j, s);
-  else orth_launch_t<VT, B, 2>(p, J, j, s);
+static void orth_launch_b(const OrthPlan& p, int J, int j, bool pend_in, bool defer, cudaStream_t s) {
+  if (J <= 128) orth_launch_t<VT, B, 1>(p, J, j, pend_in, defer, s);
+  else orth_launch_t<VT, B, 2>(p, J, j, pend_in, defer, s);
 }
 
-void launch_orth(const OrthPlan& p, VecType vt, int J, int j, int B, cudaStream_t s) {
+void launch_orth(const OrthPlan& p, VecType vt, int J, int j, int B, bool pend_in, bool defer, cudaStream_t s) {
   if (J > 256) fail(SFAIRSC_ERR_UNSUPPORTED, "Krylov basis larger than 256 columns");
   if ((J & 3) + B > 4) fail(SFAIRSC_ERR_UNSUPPORTED, "a new block must fit in one 4-column panel");
+  if ((pend_in || defer) && (j < 0 || !p.pend)) fail(SFAIRSC_ERR_INVALID_ARG, "deferred projection needs a step and a buffer");
   if (vt == VecType::F64) {
-    if (B == 1) orth_launch_b<double, 1>(p, J, j, s);
-    else if (B == 2) orth_launch_b<double, 2>(p, J, j, s);
-    else orth_launch_b<double, 4>(p, J, j, s);
+    if (B == 1) orth_launch_b<double, 1>(p, J, j, pend_in, defer, s);
+    else if (B == 2) orth_launch_b<double, 2>(p, J, j, pend_in, defer, s);
+    else orth_launch_b<double, 4>(p, J, j, pend_in, defer, s);
   } else {
-    if (B == 1) orth_launch_b<float, 1>(p, J, j, s);
-    else if (B == 2) orth_launch_b<float, 2>(p, J, j, s);
-    else orth_launch_b<float, 4>(p, J, j, s);
+    if (B == 1) orth_launch_b<float, 1>(p, J, j, pend_in, defer, s);
+    else if (B == 2) orth_launch_b<float, 2>(p, J, j, pend_in, defer, s);
+    else orth_launch_b<float, 4>(p, J, j, pend_in, defer, s);
   }
 }
 

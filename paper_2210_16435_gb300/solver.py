@@ -28,7 +28,8 @@ class FairSC:
                  prec: str = "mixed", block: int = 1, tol: float = 1e-6, basis: int = 0, max_restarts: int = 200,
                  sigma: float | None = None, seed: int = 1, kmeans_seed: int = 0, kmeans_n_init: int = 1,
                  kmeans_max_iter: int = 100, validate: int = 1, profile: int = 0, wait_limit_us: int = 0,
-                 fault_inject: int = 0, stream: torch.cuda.Stream | None = None):
+                 fault_inject: int = 0, spmv_window: int = 0, orth_mode: int = 0,
+                 stream: torch.cuda.Stream | None = None):
         self._keep = [t.contiguous() for t in (row_ptr, col_idx, values, groups)]
         row_ptr, col_idx, values, groups = self._keep
         if row_ptr.dtype != torch.int32 or col_idx.dtype != torch.int32 or groups.dtype != torch.int32:
@@ -44,7 +45,7 @@ class FairSC:
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         opts = B.make_opts(prec, block, tol, basis, max_restarts, sigma, seed, kmeans_seed, kmeans_n_init,
-                           kmeans_max_iter, validate, profile, wait_limit_us, fault_inject)
+                           kmeans_max_iter, validate, profile, wait_limit_us, fault_inject, spmv_window, orth_mode)
         self.ctx = B.sfairsc_create(self.n, self.nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(values), _DTYPES[values.dtype],
                                     _ptr(groups), self.h, self.k, 1 if normalized else 0, opts,
                                     self.stream.cuda_stream)

@@ -27,11 +27,12 @@ def eig_rel_err(got, ref, sigma, tol):
     return rel.max()
 
 
-def solve_and_check(g, k, prec, block=1, lam_tol=None, normalized=True, ref=None, vdt=torch.float64, basis=0):
+def solve_and_check(g, k, prec, block=1, lam_tol=None, normalized=True, ref=None, vdt=torch.float64, basis=0,
+                    **opts):
     from paper_2210_16435_gb300.solver import FairSC
 
     rp, ci, v, gr = graph_tensors(g, vdt)
-    s = FairSC(rp, ci, v, gr, k=k, h=g.h, prec=prec, block=block, normalized=normalized, basis=basis)
+    s = FairSC(rp, ci, v, gr, k=k, h=g.h, prec=prec, block=block, normalized=normalized, basis=basis, **opts)
     lam, H, lab, info = s.solve()
     lam, H, lab = lam.cpu().numpy(), H.cpu().numpy(), lab.cpu().numpy()
     W = sp.csr_matrix((v.double().cpu().numpy(), g.col_idx, g.row_ptr), shape=(g.n, g.n))
@@ -192,3 +193,19 @@ def test_errors_are_reported(built_lib):
     with pytest.raises(B.SFairSCError) as e:
         FairSC(rp, ci, v, gr, k=g.n, h=2)
     assert e.value.status == -5
+
+
+@pytest.mark.parametrize("block", [1, 2, 4])
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_deferred_second_projection(built_lib, prec, block):
+    """Both reorthogonalisation modes reach the oracle's pairs; the deferred one (default) passes over
+    the basis twice per step, the DGKS one up to three times."""
+    g = configs.msbm_n50k_k20_h5(scale=0.1)["graph"]
+    ref_l, ref_X = smallest_eigenpairs(operator_from_graph(g), 21, tol=1e-13, method="eigsh")
+    d = problem.degrees(g.to_scipy())
+    ref = (ref_l, ref_X / np.sqrt(d)[:, None])
+    _, _, _, i0 = solve_and_check(g, 20, prec, block=block, vdt=torch.float32, ref=ref, orth_mode=0)
+    _, _, _, i1 = solve_and_check(g, 20, prec, block=block, vdt=torch.float32, ref=ref, orth_mode=1)
+    # every launch after a block's first: two sweeps; the start / fresh-block launches may take three
+    assert i0["orth_sweeps"] <= 2 * i0["n_orth"] + (i0["restarts"] + 1), i0
+    assert i1["orth_sweeps"] >= i0["orth_sweeps"] or i1["matvecs"] != i0["matvecs"]
