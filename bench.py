@@ -542,6 +542,94 @@ def backward_bench(dev, peak):
             "fd_check": "tests/test_gpu_backward.py::test_differentiation_workload_full_size"}
 
 
+def _timed_solve(FairSC, args, kw, reps=3):
+    """Median wall time of create + solve (labels included) after one untimed run."""
+    import torch
+
+    def once():
+        s = FairSC(*args, **kw)
+        out = s.solve()
+        s.close()
+        return out
+
+    once()
+    ts = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = once()
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    return statistics.median(ts), out
+
+
+def random_laplacian_bench(dev):
+    """Exp. 4: random sparse W (mean degree 100, weights U(0, 1]) and a random dense F (h = 5), n from
+    5,000 to 10,000, k in {5, 8, 10}: time of s-FairSC (dense-constraint context) and of SC (no
+    constraint) on the GPU, FP64, residual 1e-6 sigma."""
+    import numpy as np
+    import torch
+
+    from msbm import configs
+    from paper_2210_16435_gb300.solver import FairSC
+
+    rows = []
+    for n in (5000, 7500, 10000):
+        c = configs.random_laplacian(n, 5, seed=1)
+        g, F = c["graph"], c["F"]
+        T = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+        args = (T(g.row_ptr, torch.int32), T(g.col_idx, torch.int32), T(g.values, torch.float64))
+        zero = torch.zeros(g.n, dtype=torch.int32, device=dev)
+        Ft = T(F, torch.float64)
+        for k in (5, 8, 10):
+            t_fair, (_, _, _, inf) = _timed_solve(FairSC, args + (None,), dict(k=k, prec="fp64", F=Ft))
+            t_sc, (_, _, _, inf0) = _timed_solve(FairSC, args + (zero,), dict(k=k, h=1, prec="fp64"))
+            rows.append({"n": n, "k": k, "nnz": g.nnz, "sfairsc_s": t_fair, "sc_s": t_sc, "ratio": t_fair / t_sc,
+                         "sfairsc_matvecs": inf["matvecs"], "sc_matvecs": inf0["matvecs"],
+                         "fairness_err": inf["fairness_err"]})
+    return {"workload": "random Laplacian (mean degree 100), random dense F with h = 5 (Exp. 4)", "rows": rows}
+
+
+def paper_msbm_bench(dev, sizes=(1000, 2000, 4000, 10000), fairsc_max_n=2000):
+    """Exp. 1 / App. C: m-SBM with k = 5, h in {2, 5, 10}, probabilities (10, 7, 4, 1) (log n / n)^(2/3):
+    error rate (eq. err) and average balance (eq. avebal) of s-FairSC and SC on the GPU (FP64,
+    k-means with 10 replicates) and of the oracle's dense FairSC (Algorithm 2) on the host up to
+    n = fairsc_max_n, with the times of each."""
+    import numpy as np
+    import torch
+
+    from msbm import configs
+    from oracle import fairsc
+    from oracle.kmeans import kmeans as oracle_kmeans
+    from oracle.metrics import average_balance, error_rate
+    from paper_2210_16435_gb300.solver import FairSC
+
+    rows = []
+    for h in (2, 5, 10):
+        for n in sizes:
+            c = configs.paper_msbm(n, h)
+            g, k = c["graph"], c["k"]
+            T = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+            args = (T(g.row_ptr, torch.int32), T(g.col_idx, torch.int32), T(g.values, torch.float64))
+            kw = dict(k=k, prec="fp64", kmeans_n_init=10, kmeans_max_iter=300)
+            t_fair, (_, _, lab, _) = _timed_solve(FairSC, args + (T(g.groups, torch.int32),), dict(kw, h=h))
+            t_sc, (_, _, lab_sc, _) = _timed_solve(FairSC, args + (T(g.groups * 0, torch.int32),), dict(kw, h=1))
+            lab, lab_sc = lab.cpu().numpy(), lab_sc.cpu().numpy()
+            row = {"n": n, "h": h, "nnz": g.nnz, "sfairsc_gpu_s": t_fair, "sc_gpu_s": t_sc,
+                   "err_sfairsc": error_rate(lab, g.clusters, k), "err_sc": error_rate(lab_sc, g.clusters, k),
+                   "bal_sfairsc": average_balance(lab, g.groups, k, h),
+                   "bal_sc": average_balance(lab_sc, g.groups, k, h)}
+            if n <= fairsc_max_n:
+                t0 = time.perf_counter()
+                _, Hf = fairsc.fairsc_dense(g.to_scipy(), g.groups, h, k)
+                lf, _, _ = oracle_kmeans(Hf, k, seed=0, n_init=10, max_iter=300)
+                row["fairsc_host_s"] = time.perf_counter() - t0
+                row["err_fairsc"] = error_rate(lf, g.clusters, k)
+                row["bal_fairsc"] = average_balance(lf, g.groups, k, h)
+            rows.append(row)
+    return {"workload": "m-SBM k = 5, h in {2, 5, 10}, (a, b, c, d) = (10, 7, 4, 1) (log n / n)^(2/3)", "rows": rows}
+
+
 def cpu_baseline(args, c, FairSC, rp, ci, v, gr, kw):
     """The oracle on the host cores at the bench workload: setup + its own Lanczos to
     1e-6 sigma (complete, timed, all threads) + embedding + k-means (seeding and three
@@ -718,9 +806,9 @@ def run_ours(args):
         s = FairSC(rp, ci, v, gr, k=k, h=h, prec=args.prec, block=args.block)
         opx = time_operator(B, s, dev, stream, g, s_v, s_x, (1, 4), peak)
         s.close()
-        # the same without shared-memory windows (every gather from L2), for comparison
-        s = FairSC(rp, ci, v, gr, k=k, h=h, prec=args.prec, block=args.block, spmv_window=-1)
-        line["operator_no_window"] = time_operator(B, s, dev, stream, g, s_v, s_x, (1, 4), peak)
+        # the same with shared-memory windows of the input vector (static row ranges), for comparison
+        s = FairSC(rp, ci, v, gr, k=k, h=h, prec=args.prec, block=args.block, spmv_window=1)
+        line["operator_windows"] = time_operator(B, s, dev, stream, g, s_v, s_x, (1, 4), peak)
         s.close()
         line["operator"] = opx
         # plain FP64 GPU path on the same graph, block 1 and block 4 (block 4 isolates the precision effect)
@@ -743,6 +831,10 @@ def run_ours(args):
         line["h_sweep"] = h_sweep(FairSC, B, dev, stream, g, rp, ci, v, k, h, args, s_v, s_x, peak)
         # differentiation form: gradient of the sum of the 10 smallest eigenvalues at n = 200,000
         line["backward"] = backward_bench(dev, peak)
+        # Exp. 4: random Laplacian with a random dense F, s-FairSC against SC on the GPU
+        line["random_laplacian"] = random_laplacian_bench(dev)
+        # Exp. 1 / App. C: the experiments' m-SBM, s-FairSC and SC on the GPU, FairSC on the host
+        line["paper_msbm"] = paper_msbm_bench(dev)
         # end to end through the C ABI with host buffers: copies inside the timed region
         hp = [torch.as_tensor(np.ascontiguousarray(a), dtype=dt).pin_memory()
               for a, dt in ((g.row_ptr, torch.int32), (g.col_idx, torch.int32), (g.values, vdt),

@@ -99,9 +99,11 @@ typedef struct {
                               sfairsc_solve / sfairsc_apply_operator call waits on a device flag that
                               nothing sets, so that call ends in DEVICE_TIMEOUT after wait_limit_us
                               (no fault, no hang); the hook is then cleared and later calls run normally */
-  int32_t spmv_window;     /* 0: the operator's SpMV stages, per row segment, a slice of its input vector
-                              in shared memory where that serves enough of the segment's gathers (chosen
-                              at create from the column distribution); -1: never (every gather from L2) */
+  int32_t spmv_window;     /* 0 (default): the operator's SpMV takes row blocks dynamically and gathers
+                              its input from L2.  1: each CTA keeps its own row range and, per row
+                              segment, stages a slice of the input vector in shared memory where that
+                              serves enough of the segment's gathers (chosen at create from the column
+                              distribution), gathering the rest from L2 */
   int32_t orth_mode;       /* reorthogonalisation of each new Krylov block.  0: classical Gram-Schmidt
                               twice with the second projection deferred -- the block is stored after one
                               projection and corrected during the next step's first pass over the basis
@@ -184,6 +186,27 @@ SFAIRSC_API int sfairsc_create(sfairsc_ctx** out, int64_t n, int64_t nnz, const 
                    const void* values, int32_t value_dtype, const int32_t* group_labels, int32_t h, int32_t k,
                    int32_t normalized, const sfairsc_opts* opts, void* cuda_stream);
 
+/*
+ * A context for the fair SC problem with a general constraint matrix F in place of group labels
+ * (eq. normal-prob-fair: min tr(H^T L H), H^T D H = I, F^T H = 0, for any F of full column rank;
+ * the random-Laplacian experiment of Sec. 4 uses a random dense F).  Everything else is as in
+ * sfairsc_create: C = D^{-1/2} F (F for normalized = 0), C^T C = F^T D^{-1} F is formed by a
+ * device reduction and factored in FP64 (Sec. 3.4 (ii), eq. mv-Pw), and the fused operator
+ * applies P w = w - C (C^T C)^{-1} C^T w as a pair of tall-skinny products (C^T w reduced over
+ * the rows, then C a per row) around the SpMV.  sfairsc_solve, sfairsc_apply_operator,
+ * sfairsc_backward work on the context unchanged; info.fairness_err is max |F^T H|.
+ *
+ * F  double[n * p], row-major (row i holds F's row i), DEVICE or host memory; borrowed if on
+ *    the device (keep it alive and unchanged until destroy), copied if on the host.  Finite.
+ * p  columns of F, 0..31 (0: no constraint, plain SC, Algorithm 1); k <= n - p.
+ * Errors: as sfairsc_create; INVALID_ARG also when F lacks full column rank (its C^T C is not
+ * positive definite), NONFINITE when F holds a non-finite entry; UNSUPPORTED for p > 31.
+ */
+SFAIRSC_API int sfairsc_create_dense(sfairsc_ctx** out, int64_t n, int64_t nnz, const int32_t* row_ptr,
+                                     const int32_t* col_idx, const void* values, int32_t value_dtype, const double* F,
+                                     int32_t p, int32_t k, int32_t normalized, const sfairsc_opts* opts,
+                                     void* cuda_stream);
+
 /* Release the context and its workspace.  NULL is accepted.  Returns OK or CUDA. */
 SFAIRSC_API int sfairsc_destroy(sfairsc_ctx* ctx);
 
@@ -243,6 +266,33 @@ SFAIRSC_API int sfairsc_kmeans(int64_t n, int32_t d, const double* X, int32_t kc
  */
 SFAIRSC_API int sfairsc_backward(sfairsc_ctx* ctx, const double* grad_lambda, double* grad_values, double bandwidth,
                      double* grad_bandwidth);
+
+/*
+ * Gradient of a loss on the embedding H (and optionally on the eigenvalues) with respect to the
+ * stored weights, after a successful sfairsc_solve on this context (normalized problem, k <= 64,
+ * simple eigenvalues).  The columns of H are the generalized eigenvectors of the pencil
+ * (Z^T L Z, Z^T D Z) of Algorithm 2 (Z spans null(F^T) and does not depend on W), with H^T D H = I
+ * and the sign convention of sfairsc_solve; first-order perturbation gives, per undirected weight,
+ *   d loss / d w_ab = sum_i (v_ia - v_ib)(h_ia - h_ib) - lambda_i (v_ia h_ia + v_ib h_ib)
+ *                           - c_i (h_ia^2 + h_ib^2) / 2
+ *                   + sum_i gbar_lambda_i ((h_ia - h_ib)^2 - lambda_i (h_ia^2 + h_ib^2)),
+ * v_i = sum_{j != i} h_j (h_j^T gbar_i) / (lambda_i - lambda_j) over every eigenpair of the pencil,
+ * c_i = gbar_i^T h_i.  The j <= k part of v_i comes from the computed eigenvectors; the rest from k
+ * conjugate-gradient solves (A - lambda_i I) y = (I - X X^T) P D^{-1/2} gbar_i on the FP64 operator
+ * A = L_n^sigma, positive definite on that complement; then one SDDMM over W's pattern.
+ * Each CSR entry receives half of the undirected derivative.
+ * grad_H        double[n * k] row-major (d loss / d H), device or host
+ * grad_lambda   double[k] or NULL
+ * grad_values   double[nnz] output, device or host
+ * bandwidth, grad_bandwidth   as in sfairsc_backward
+ * max_iter      conjugate-gradient iterations (0: 1000); rtol relative residual (<= 0: 1e-10)
+ * iterations, max_rel_resid   (nullable) iterations taken and the largest final relative residual
+ * Errors: INVALID_ARG (no solve, repeated eigenvalue), UNSUPPORTED (k > 64, normalized = 0), CUDA, OOM,
+ * DEVICE_TIMEOUT.
+ */
+SFAIRSC_API int sfairsc_backward_vectors(sfairsc_ctx* ctx, const double* grad_H, const double* grad_lambda,
+                                         double* grad_values, double bandwidth, double* grad_bandwidth,
+                                         int32_t max_iter, double rtol, int32_t* iterations, double* max_rel_resid);
 
 /*
  * One application of L_n^sigma (same result as sfairsc_apply_operator in

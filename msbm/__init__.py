@@ -19,6 +19,8 @@ from .generator import (
     sample_msbm,
     gaussian_edge_weights,
     graph_from_dense,
+    random_constraints,
+    random_weighted_graph,
 )
 from . import configs
 
@@ -30,5 +32,7 @@ __all__ = [
     "sample_msbm",
     "gaussian_edge_weights",
     "graph_from_dense",
+    "random_weighted_graph",
+    "random_constraints",
     "configs",
 ]

@@ -17,6 +17,9 @@ Workloads (sizes as named):
   msbm_n200k_k10_h4_gauss n = 200,000, 10 clusters, 4 groups, mean degree 48,
                           Gaussian-kernel weights exp(-r^2 / (2 s^2)), s = 2,
                           16-d features, seed 4
+  random_laplacian(n, h)  the random-Laplacian workload (Exp. 4): random sparse
+                          symmetric W (density 100 / n, weights U(0, 1]) and a
+                          dense random constraint matrix F (n x (h-1), U[0, 1))
   paper_msbm(n, h)        the experiments' m-SBM (Exp. 1, App. C): k = 5 equal
                           clusters, h equal groups, probabilities
                           (a, b, c, d) = (10, 7, 4, 1) (log n / n)^(2/3) with
@@ -28,6 +31,8 @@ from __future__ import annotations
 import numpy as np
 
 from .generator import (
+    random_constraints,
+    random_weighted_graph,
     cell_sizes_equal,
     cell_sizes_from_proportions,
     category_probabilities,
@@ -115,6 +120,16 @@ def paper_msbm(n: int, h: int, k: int = 5, seed: int = 0):
              (True, False): min(1.0, 4 * base), (False, False): min(1.0, base)}
     g = sample_msbm(cells, probs, seed=seed * 1000 + 7 * h + n % 997)
     return {"name": f"paper_msbm_n{n}_h{h}", "graph": g, "k": k, "h": h, "value_dtype": "f64", "prec": "fp64"}
+
+
+def random_laplacian(n: int, h: int = 5, k: int = 5, mean_degree: float = 100.0, seed: int = 0):
+    """The random-Laplacian workload of Exp. 4: a random sparse symmetric W and a random dense F
+    (the paper does not state the sparsity of this experiment; mean degree 100 is this build's
+    reading)."""
+    g = random_weighted_graph(n, min(1.0, mean_degree / (n - 1)), seed=seed * 1000 + 11)
+    F = random_constraints(n, h - 1, seed=seed * 1000 + 12)
+    return {"name": f"random_laplacian_n{n}_h{h}", "graph": g, "F": F, "k": k, "h": h, "value_dtype": "f64",
+            "prec": "fp64"}
 
 
 BUILDERS = {

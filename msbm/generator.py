@@ -268,6 +268,31 @@ def sample_msbm(cells, probs: dict, seed: int, max_attempts: int = 8, allow_isol
     raise RuntimeError(f"m-SBM draw kept an isolated vertex after {max_attempts} attempts")
 
 
+def random_weighted_graph(n: int, density: float, seed: int, max_attempts: int = 8) -> Graph:
+    """A random symmetric sparse weight matrix (the random-Laplacian workload, Sec. 4 datasets):
+    every unordered pair of distinct vertices is an edge with probability `density`, with a
+    weight drawn uniformly from (0, 1]; no self loops; redrawn (seed * 2**32 + attempt) while a
+    vertex is isolated.  There is no cluster structure: groups and clusters are all zero."""
+    cells = np.array([[n]], dtype=np.int64)
+    for attempt in range(max_attempts):
+        s = seed if attempt == 0 else seed * 2**32 + attempt
+        rng = np.random.default_rng(s)
+        i, j = _sample_pairs(rng, cells, {(True, True): density})
+        deg = np.bincount(i, minlength=n) + np.bincount(j, minlength=n)
+        if (deg > 0).all():
+            w = 1.0 - rng.random(i.size)  # (0, 1]
+            row_ptr, col, vals = _to_csr(n, i, j, w)
+            z = np.zeros(n, dtype=np.int32)
+            return Graph(row_ptr, col, vals, z, z.copy(), 1, 1, meta={"seed": int(s), "density": density})
+    raise RuntimeError(f"random graph kept an isolated vertex after {max_attempts} attempts")
+
+
+def random_constraints(n: int, p: int, seed: int) -> np.ndarray:
+    """A dense n x p constraint matrix with entries uniform in [0, 1) (the random-Laplacian
+    experiment's F, a placeholder without group meaning); full column rank with probability 1."""
+    return np.random.default_rng(seed).random((n, p))
+
+
 def gaussian_edge_weights(g: Graph, dim: int, mean_scale: float, bandwidth: float, seed: int):
     """Gaussian-kernel weights on the graph's pattern.
 

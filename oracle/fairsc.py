@@ -35,11 +35,13 @@ def nullspace_basis(F: np.ndarray) -> np.ndarray:
     return U[:, rank:]
 
 
-def fairsc_dense(W, groups, h: int, k: int):
-    """Algorithm 2 (FairSC).  Returns (eigenvalues[k], H[n, k])."""
+def fairsc_dense(W, groups, h: int, k: int, F=None):
+    """Algorithm 2 (FairSC).  Returns (eigenvalues[k], H[n, k]).  F: a dense constraint matrix
+    (n x (h-1)) in place of the group constraints."""
     L = _dense(laplacian(W))
     D = np.diag(degrees(W))
-    _, F, _ = fairness_constraints(groups, h)
+    if F is None:
+        _, F, _ = fairness_constraints(groups, h)
     Z = nullspace_basis(F)                                   # step 2
     mu, E = np.linalg.eigh(Z.T @ D @ Z)                      # step 3: Q = (Z^T D Z)^{1/2}
     Qinv = (E / np.sqrt(mu)) @ E.T                           #         Q^{-1}
@@ -69,14 +71,14 @@ def projector(C: np.ndarray) -> np.ndarray:
     return np.eye(n) - C @ np.linalg.solve(C.T @ C, C.T)
 
 
-def sfairsc_matrix(W, groups, h: int, sigma: float | None = None, normalized: bool = True):
+def sfairsc_matrix(W, groups, h: int, sigma: float | None = None, normalized: bool = True, F=None):
     """The explicit L_n^sigma = P L_n P + sigma (I - P) (eq. asigma) and its sigma.
 
     sigma defaults to ||L_n||_1 (App. C).  normalized=False uses L and
     P = I - F (F^T F)^{-1} F^T, an extension the paper does not define.
     """
     A = _dense(normalized_laplacian(W) if normalized else laplacian(W))
-    C = constraint_matrix(W, groups, h, normalized)
+    C = constraint_matrix(W, groups, h, normalized, F)
     P = projector(C)
     if sigma is None:
         sigma = sigma_one_norm(A)
@@ -85,12 +87,12 @@ def sfairsc_matrix(W, groups, h: int, sigma: float | None = None, normalized: bo
     return 0.5 * (As + As.T), sigma
 
 
-def sfairsc_dense(W, groups, h: int, k: int, sigma: float | None = None, normalized: bool = True):
+def sfairsc_dense(W, groups, h: int, k: int, sigma: float | None = None, normalized: bool = True, F=None):
     """k smallest eigenpairs of the dense L_n^sigma, H = D^{-1/2} X (Algorithm 3).
 
     Returns (eigenvalues[k], H[n, k], X[n, k], sigma, all eigenvalues).
     """
-    As, sigma = sfairsc_matrix(W, groups, h, sigma, normalized)
+    As, sigma = sfairsc_matrix(W, groups, h, sigma, normalized, F)
     lam, X = np.linalg.eigh(As)
     Xk = X[:, :k]
     H = Xk / np.sqrt(degrees(W))[:, None] if normalized else Xk

@@ -56,9 +56,15 @@ def fairness_constraints(groups, h: int):
     return F0, F0[:, : h - 1], z
 
 
-def constraint_matrix(W, groups, h: int, normalized: bool = True) -> np.ndarray:
-    """C = D^{-1/2} F (Sec. 3.2) for the normalized problem, F itself otherwise."""
-    _, F, _ = fairness_constraints(groups, h)
+def constraint_matrix(W, groups, h: int, normalized: bool = True, F=None) -> np.ndarray:
+    """C = D^{-1/2} F (Sec. 3.2) for the normalized problem, F itself otherwise.
+
+    F defaults to the group constraints of Lemma 2.1; a dense F (n x (h-1), full
+    column rank) stands for any other linear constraint F^T H = 0 (the random
+    Laplacian experiment, where F is a random matrix)."""
+    if F is None:
+        _, F, _ = fairness_constraints(groups, h)
+    F = np.asarray(F, dtype=np.float64)
     if not normalized:
         return F
     return F / np.sqrt(degrees(W))[:, None]

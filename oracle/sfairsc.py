@@ -20,7 +20,8 @@ from .problem import adjacency, constraint_matrix, degrees, laplacian, normalize
 class SFairSCOperator:
     """w -> L_n^sigma w for the graph W and group labels (eq. asigma, Sec. 3.4)."""
 
-    def __init__(self, W, groups, h: int, sigma: float | None = None, normalized: bool = True):
+    def __init__(self, W, groups, h: int, sigma: float | None = None, normalized: bool = True, F=None):
+        """F: a dense n x (h-1) constraint matrix in place of the group constraints (groups unused)."""
         self.W = W
         self.n = W.shape[0]
         self.h = h
@@ -29,7 +30,7 @@ class SFairSCOperator:
         if np.any(self.d <= 0):
             raise ValueError("isolated vertex (Sec. 2.1 assumes D > 0)")
         self.A = normalized_laplacian(W) if normalized else laplacian(W).tocsr()
-        self.C = constraint_matrix(W, groups, h, normalized)
+        self.C = constraint_matrix(W, groups, h, normalized, F)
         self.chol = sla.cho_factor(self.C.T @ self.C) if h > 1 else None   # Lemma 2.1: C^T C is SPD
         self.sigma = sigma_one_norm(self.A) if sigma is None else float(sigma)
 

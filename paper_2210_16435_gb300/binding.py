@@ -106,12 +106,16 @@ def load(path: str | None = None):
     lib.sfairsc_opts_default.argtypes = [ctypes.POINTER(Opts)]
     lib.sfairsc_create.argtypes = [ctypes.POINTER(vp), i64, i64, vp, vp, vp, i32, vp, i32, i32, i32,
                                    ctypes.POINTER(Opts), vp]
+    lib.sfairsc_create_dense.argtypes = [ctypes.POINTER(vp), i64, i64, vp, vp, vp, i32, vp, i32, i32, i32,
+                                         ctypes.POINTER(Opts), vp]
     lib.sfairsc_destroy.argtypes = [vp]
     lib.sfairsc_get_sigma.argtypes = [vp, ctypes.POINTER(dbl)]
     lib.sfairsc_apply_operator.argtypes = [vp, vp, vp, i32]
     lib.sfairsc_solve.argtypes = [vp, vp, vp, vp, ctypes.POINTER(Info)]
     lib.sfairsc_kmeans.argtypes = [i64, i32, vp, i32, u64, i32, i32, vp, vp, vp, vp, vp]
     lib.sfairsc_backward.argtypes = [vp, vp, vp, dbl, vp]
+    lib.sfairsc_backward_vectors.argtypes = [vp, vp, vp, vp, dbl, vp, i32, dbl, ctypes.POINTER(i32),
+                                             ctypes.POINTER(dbl)]
     lib.sfairsc_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(BatchGraph), ctypes.POINTER(Opts),
                                          vp]
     lib.sfairsc_batch_autotune.argtypes = [vp]
@@ -121,8 +125,8 @@ def load(path: str | None = None):
     lib.sfairsc_batch_stats.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(dbl)]
     lib.sfairsc_solve_batched.argtypes = [i32, ctypes.POINTER(BatchGraph), ctypes.POINTER(Opts),
                                           ctypes.POINTER(i32), ctypes.POINTER(BatchInfo), vp]
-    for f in ("sfairsc_opts_default", "sfairsc_create", "sfairsc_destroy", "sfairsc_get_sigma",
-              "sfairsc_apply_operator", "sfairsc_solve", "sfairsc_kmeans", "sfairsc_backward",
+    for f in ("sfairsc_opts_default", "sfairsc_create", "sfairsc_create_dense", "sfairsc_destroy", "sfairsc_get_sigma",
+              "sfairsc_apply_operator", "sfairsc_solve", "sfairsc_kmeans", "sfairsc_backward", "sfairsc_backward_vectors",
               "sfairsc_batch_create", "sfairsc_batch_autotune", "sfairsc_batch_schedule", "sfairsc_batch_solve", "sfairsc_batch_destroy", "sfairsc_batch_stats",
               "sfairsc_solve_batched"):
         getattr(lib, f).restype = ctypes.c_int
@@ -157,6 +161,17 @@ def sfairsc_create(n, nnz, row_ptr, col_idx, values, value_dtype, group_labels, 
     return ctx.value
 
 
+def sfairsc_create_dense(n, nnz, row_ptr, col_idx, values, value_dtype, F, p, k, normalized=1, opts=None,
+                         stream=None) -> int:
+    """Context with a dense constraint matrix F (n x p row-major FP64 address) in place of labels."""
+    ctx = ctypes.c_void_p()
+    rc = load().sfairsc_create_dense(ctypes.byref(ctx), int(n), int(nnz), row_ptr, col_idx, values, int(value_dtype),
+                                     F, int(p), int(k), int(normalized),
+                                     ctypes.byref(opts) if opts is not None else None, stream)
+    _check(rc, "sfairsc_create_dense")
+    return ctx.value
+
+
 def sfairsc_destroy(ctx) -> None:
     _check(load().sfairsc_destroy(ctx), "sfairsc_destroy")
 
@@ -185,6 +200,19 @@ def sfairsc_kmeans(n, d, X, kc, seed, n_init, max_iter, labels, centroids=None, 
                                ctypes.byref(inertia), ctypes.byref(iters), stream)
     _check(rc, "sfairsc_kmeans")
     return inertia.value, iters.value
+
+
+def sfairsc_backward_vectors(ctx, grad_H, grad_lambda, grad_values, bandwidth=0.0, want_bandwidth=False, max_iter=0,
+                             rtol=0.0):
+    """Returns (d loss / d bandwidth or None, CG iterations, largest final relative residual)."""
+    gs = ctypes.c_double()
+    it = ctypes.c_int32()
+    rr = ctypes.c_double()
+    rc = load().sfairsc_backward_vectors(ctx, grad_H, grad_lambda, grad_values, float(bandwidth),
+                                         ctypes.byref(gs) if want_bandwidth else None, int(max_iter), float(rtol),
+                                         ctypes.byref(it), ctypes.byref(rr))
+    _check(rc, "sfairsc_backward_vectors")
+    return (gs.value if want_bandwidth else None), it.value, rr.value
 
 
 def sfairsc_backward(ctx, grad_lambda, grad_values, bandwidth=0.0, want_bandwidth=False):

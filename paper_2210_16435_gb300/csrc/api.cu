@@ -122,11 +122,15 @@ struct sfairsc_ctx {
   int diag_blocks = 0;
   double* bw_partial = nullptr;
   double* bw_A = nullptr;
+  double* bw_Hp = nullptr;  // H with rows padded for the backward gathers
   int bw_blocks = 0;
   int32_t* labels_d = nullptr;
   std::vector<double> lam_h;
   bool solved = false;
   bool fault_pending = false;
+  const double* Fd64 = nullptr;  // dense constraints (n x (h - 1) row-major FP64), or null: group labels
+  float* Fd32 = nullptr;         // its FP32 copy (MIXED)
+  double* fth_partial = nullptr; // per-block F^T H (dense constraints)
   bool shift_found = false;    // the last final check met a Ritz vector in range(C)  // opts.fault_inject: the next operator launch waits on a flag nothing sets
   // live kernel timing (opts.profile) and launch counting
   std::vector<cudaEvent_t> ev_pool;
@@ -206,7 +210,10 @@ int next_pow2(int x) {
 }
 
 void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_idx, const void* values,
-                   const int32_t* labels) {
+                   const int32_t* labels, const double* F = nullptr) {
+  // dense constraints (F given): no groups; the label passes run with one group of all vertices
+  const bool dense = F != nullptr;
+  const int hl = dense ? 1 : c->h;
   cudaStream_t s = c->stream;
   const int n = (int)c->n;
   int dev = 0;
@@ -219,12 +226,20 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   c->row_ptr = to_device(c, row_ptr, (size_t)n + 1);
   c->col = to_device(c, col_idx, (size_t)c->nnz);
   c->val_orig = to_device(c, static_cast<const unsigned char*>(values), (size_t)c->nnz, dtype_size(c->vdt_orig));
-  const int32_t* lab_in = to_device(c, labels, (size_t)n);
+  const int32_t* lab_in = nullptr;
+  if (dense) {
+    int32_t* zl = c->dalloc<int32_t>(n);
+    check_cuda(cudaMemsetAsync(zl, 0, sizeof(int32_t) * n, s), "memset");
+    lab_in = zl;
+    c->Fd64 = to_device(c, F, (size_t)n * (c->h - 1));
+  } else {
+    lab_in = to_device(c, labels, (size_t)n);
+  }
 
   unsigned* flags = c->dalloc<unsigned>(4);
   check_cuda(cudaMemsetAsync(flags, 0, 4 * sizeof(unsigned), s), "memset");
   if (c->opts.validate > 0)
-    launch_validate(n, c->nnz, c->row_ptr, c->col, c->val_orig, c->vdt_orig, lab_in, c->h, c->opts.validate >= 2,
+    launch_validate(n, c->nnz, c->row_ptr, c->col, c->val_orig, c->vdt_orig, lab_in, hl, c->opts.validate >= 2,
                     flags, s);
   unsigned hf = 0;
   check_cuda(cudaMemcpyAsync(&hf, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "d2h");
@@ -241,11 +256,11 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   c->dinv64 = c->dalloc<double>(n);
   c->dinv32 = c->dalloc<float>(n);
   const int nb = degrees_blocks(n);
-  double* bsum = c->dalloc<double>((size_t)nb * 2 * c->h);
+  double* bsum = c->dalloc<double>((size_t)nb * 2 * hl);
   check_cuda(cudaMemsetAsync(flags, 0, sizeof(unsigned), s), "memset");
-  launch_degrees(n, c->row_ptr, c->val_orig, c->vdt_orig, lab_in, c->lab, c->deg, c->dinv64, c->dinv32, bsum, nb, c->h,
+  launch_degrees(n, c->row_ptr, c->val_orig, c->vdt_orig, lab_in, c->lab, c->deg, c->dinv64, c->dinv32, bsum, nb, hl,
                  c->normalized, flags, s);
-  std::vector<double> hb((size_t)nb * 2 * c->h);
+  std::vector<double> hb((size_t)nb * 2 * hl);
   check_cuda(cudaMemcpyAsync(hb.data(), bsum, hb.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "d2h");
   check_cuda(cudaMemcpyAsync(&hf, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s), "d2h");
   check_cuda(cudaStreamSynchronize(s), "degrees");
@@ -253,36 +268,55 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   const int h = c->h;
   std::vector<double> cnt(h, 0.0), S(h, 0.0);
   for (int b = 0; b < nb; ++b)
-    for (int g = 0; g < h; ++g) {
-      cnt[g] += hb[((size_t)b * h + g) * 2 + 0];
-      S[g] += hb[((size_t)b * h + g) * 2 + 1];
+    for (int g = 0; g < hl; ++g) {
+      cnt[g] += hb[((size_t)b * hl + g) * 2 + 0];
+      S[g] += hb[((size_t)b * hl + g) * 2 + 1];
     }
-  for (int g = 0; g < h; ++g)
-    if (cnt[g] < 0.5) fail(SFAIRSC_ERR_EMPTY_GROUP, "group " + std::to_string(g) + " is empty");
+  if (!dense)
+    for (int g = 0; g < h; ++g)
+      if (cnt[g] < 0.5) fail(SFAIRSC_ERR_EMPTY_GROUP, "group " + std::to_string(g) + " is empty");
   if (c->k > n - h + 1) fail(SFAIRSC_ERR_K_TOO_LARGE, "k exceeds n - h + 1");
 
   // C^T C in closed form and its Cholesky factor (Lemma 2.1: SPD)
   c->z.assign(h, 0.0);
   double Ssum = 0.0;
-  for (int g = 0; g < h; ++g) {
-    c->z[g] = cnt[g] / (double)n;
-    Ssum += S[g];
-  }
+  if (!dense)
+    for (int g = 0; g < h; ++g) {
+      c->z[g] = cnt[g] / (double)n;
+      Ssum += S[g];
+    }
   check_cuda(cudaMallocHost((void**)&c->params_host, sizeof(double) * kParams), "pinned allocation");
   double* P = c->params_host;
   std::fill(P, P + kParams, 0.0);
   for (int g = 0; g < h; ++g) P[kPZ + g] = c->z[g];
   const int p = h - 1;
   std::vector<double> M((size_t)std::max(p, 1) * std::max(p, 1), 0.0);
-  for (int a = 0; a < p; ++a)
-    for (int b = 0; b < p; ++b)
-      M[(size_t)a * p + b] = (a == b ? S[a] : 0.0) - c->z[b] * S[a] - c->z[a] * S[b] + c->z[a] * c->z[b] * Ssum;
+  if (dense && p > 0) {
+    // C^T C = F^T D^{-1} F (F^T F unnormalized) by a device reduction, summed here in block order
+    const int cb = std::max(1, std::min(2 * c->sms, (n + 63) / 64));
+    double* part = c->dalloc<double>((size_t)cb * p * p);
+    launch_dense_ctc(n, p, c->Fd64, c->deg, c->normalized, part, cb, s);
+    std::vector<double> hp((size_t)cb * p * p);
+    check_cuda(cudaMemcpyAsync(hp.data(), part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "d2h");
+    check_cuda(cudaStreamSynchronize(s), "C^T C");
+    for (int b = 0; b < cb; ++b)
+      for (int q = 0; q < p * p; ++q) M[q] += hp[(size_t)b * p * p + q];
+    for (double v : M)
+      if (!std::isfinite(v)) fail(SFAIRSC_ERR_NONFINITE, "non-finite entry in F");
+  } else {
+    for (int a = 0; a < p; ++a)
+      for (int b = 0; b < p; ++b)
+        M[(size_t)a * p + b] = (a == b ? S[a] : 0.0) - c->z[b] * S[a] - c->z[a] * S[b] + c->z[a] * c->z[b] * Ssum;
+  }
   for (int a = 0; a < p; ++a) {
     for (int b = 0; b <= a; ++b) {
       double sum = M[(size_t)a * p + b];
       for (int q = 0; q < b; ++q) sum -= P[kPL + a * kLStride + q] * P[kPL + b * kLStride + q];
       if (a == b) {
-        if (!(sum > 0.0)) fail(SFAIRSC_ERR_EMPTY_GROUP, "C^T C is not positive definite");
+        if (!(sum > 0.0))
+          fail(dense ? SFAIRSC_ERR_INVALID_ARG : SFAIRSC_ERR_EMPTY_GROUP,
+               dense ? "F does not have full column rank (C^T C is not positive definite)"
+                     : "C^T C is not positive definite");
         P[kPL + a * kLStride + a] = std::sqrt(sum);
       } else {
         P[kPL + a * kLStride + b] = sum / P[kPL + b * kLStride + b];
@@ -378,10 +412,21 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   c->op64.dinv = c->dinv64;
   c->op64.ytil = c->ytil64;
   c->op64.lanes_per_row = lanes_for(4.0);
+  if (dense && c->h > 1) {
+    if (c->vt == VecType::F32) {
+      float* f32 = c->dalloc<float>((size_t)n * (c->h - 1));
+      launch_f64_to_f32((int64_t)n * (c->h - 1), c->Fd64, f32, s);
+      c->Fd32 = f32;
+      c->op.Fd = f32;
+    } else {
+      c->op.Fd = c->Fd64;
+    }
+    c->op64.Fd = c->Fd64;
+  }
   c->proj64 = c->op64;
   c->proj64.mode = 1;
   // shared-memory windows of the SpMV input, one table per block size, for both precisions
-  if (c->opts.spmv_window == 0) {
+  if (c->opts.spmv_window == 1) {
     std::vector<int32_t> rows_h(grid + 1);
     check_cuda(cudaMemcpyAsync(rows_h.data(), c->cta_rows, sizeof(int32_t) * (grid + 1), cudaMemcpyDeviceToHost, s),
                "d2h");
@@ -469,9 +514,11 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   c->colkey = c->dalloc<unsigned long long>(2 * (size_t)k);
   c->diag_blocks = std::max(1, std::min(2 * c->sms, (n + 1023) / 1024));
   c->diag_partial = c->dalloc<double>((size_t)c->diag_blocks * ((size_t)h * k + (size_t)k * k));
-  c->bw_blocks = std::max(1, std::min(4 * c->sms, (n + 7) / 8));
+  if (dense && h > 1) c->fth_partial = c->dalloc<double>((size_t)c->diag_blocks * (h - 1) * k);
+  c->bw_blocks = std::max(1, std::min(8 * c->sms, (n + 7) / 8));
   c->bw_partial = c->dalloc<double>(c->bw_blocks);
   c->bw_A = c->dalloc<double>(n);
+  c->bw_Hp = c->dalloc<double>((size_t)n * backward_padded_width(k));
   c->labels_d = c->dalloc<int32_t>(n);
   check_cuda(cudaStreamSynchronize(s), "create");
 }
@@ -832,24 +879,42 @@ int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* label
   // diagnostics: max |F^T H| and max |H^T D H - I|
   {
     const int h = c->h;
-    launch_diagnostics(n, k, h, c->Hres, c->deg, c->lab, c->params, c->diag_partial, c->diag_blocks, nullptr, s,
+    const bool dense = c->Fd64 != nullptr;
+    const int hd = dense ? 1 : h;  // dense constraints: the label sums are unused, F^T H comes below
+    launch_diagnostics(n, k, hd, c->Hres, c->deg, c->lab, c->params, c->diag_partial, c->diag_blocks, nullptr, s,
                        c->vt == VecType::F64);
-    const size_t P = (size_t)h * k + (size_t)k * k;
+    const size_t P = (size_t)hd * k + (size_t)k * k;
     std::vector<double> dg((size_t)c->diag_blocks * P);
     check_cuda(cudaMemcpyAsync(dg.data(), c->diag_partial, dg.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "d2h");
+    std::vector<double> fth;
+    if (dense && h > 1) {
+      launch_dense_fth(n, h - 1, k, c->Fd64, c->Hres, c->fth_partial, c->diag_blocks, s);
+      fth.resize((size_t)c->diag_blocks * (h - 1) * k);
+      check_cuda(cudaMemcpyAsync(fth.data(), c->fth_partial, fth.size() * sizeof(double), cudaMemcpyDeviceToHost, s),
+                 "d2h");
+    }
     check_cuda(cudaStreamSynchronize(s), "diagnostics");
     std::vector<double> acc(P, 0.0);
     for (int b = 0; b < c->diag_blocks; ++b)
       for (size_t i = 0; i < P; ++i) acc[i] += dg[(size_t)b * P + i];
     double ferr = 0.0, derr = 0.0;
-    for (int i = 0; i < k; ++i) {
-      double tot = 0.0;
-      for (int g = 0; g < h; ++g) tot += acc[(size_t)g * k + i];
-      for (int g = 0; g + 1 < h; ++g) ferr = std::max(ferr, std::fabs(acc[(size_t)g * k + i] - c->z[g] * tot));
+    if (dense) {
+      const size_t q = (size_t)(h - 1) * k;
+      for (size_t i = 0; i < q; ++i) {
+        double t = 0.0;
+        for (int b = 0; b < c->diag_blocks; ++b) t += fth[(size_t)b * q + i];
+        ferr = std::max(ferr, std::fabs(t));
+      }
+    } else {
+      for (int i = 0; i < k; ++i) {
+        double tot = 0.0;
+        for (int g = 0; g < h; ++g) tot += acc[(size_t)g * k + i];
+        for (int g = 0; g + 1 < h; ++g) ferr = std::max(ferr, std::fabs(acc[(size_t)g * k + i] - c->z[g] * tot));
+      }
     }
     for (int a = 0; a < k; ++a)
       for (int b = a; b < k; ++b) {
-        const double v = acc[(size_t)h * k + (size_t)a * k + b];
+        const double v = acc[(size_t)hd * k + (size_t)a * k + b];
         derr = std::max(derr, std::fabs(v - (a == b ? 1.0 : 0.0)));
       }
     inf.fairness_err = ferr;
@@ -927,6 +992,13 @@ int sfairsc_opts_default(sfairsc_opts* o) {
   return SFAIRSC_OK;
 }
 
+static bool valid_opts(const sfairsc_opts& o) {
+  return o.tol > 0.0 && o.max_restarts >= 0 && o.block >= 1 && o.block <= SFAIRSC_MAX_BLOCK && o.kmeans_n_init >= 1 &&
+         o.kmeans_max_iter >= 1 && (o.prec == 0 || o.prec == 1) && o.wait_limit_us >= 0 &&
+         (o.fault_inject == 0 || o.fault_inject == 1) && (o.spmv_window == 0 || o.spmv_window == 1) &&
+         (o.orth_mode == 0 || o.orth_mode == 1);
+}
+
 int sfairsc_create(sfairsc_ctx** out, int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
                    const void* values, int32_t value_dtype, const int32_t* group_labels, int32_t h, int32_t k,
                    int32_t normalized, const sfairsc_opts* opts, void* cuda_stream) {
@@ -945,10 +1017,7 @@ int sfairsc_create(sfairsc_ctx** out, int64_t n, int64_t nnz, const int32_t* row
   if (!c) return SFAIRSC_ERR_OOM;
   sfairsc_opts_default(&c->opts);
   if (opts) c->opts = *opts;
-  if (!(c->opts.tol > 0.0) || c->opts.max_restarts < 0 || c->opts.block < 1 || c->opts.block > SFAIRSC_MAX_BLOCK ||
-      c->opts.kmeans_n_init < 1 || c->opts.kmeans_max_iter < 1 || (c->opts.prec != 0 && c->opts.prec != 1) ||
-      c->opts.wait_limit_us < 0 || (c->opts.fault_inject != 0 && c->opts.fault_inject != 1) ||
-      (c->opts.spmv_window != 0 && c->opts.spmv_window != -1) || (c->opts.orth_mode != 0 && c->opts.orth_mode != 1)) {
+  if (!valid_opts(c->opts)) {
     g_last_error = "invalid options";
     return SFAIRSC_ERR_INVALID_ARG;
   }
@@ -961,6 +1030,44 @@ int sfairsc_create(sfairsc_ctx** out, int64_t n, int64_t nnz, const int32_t* row
   c->stream = static_cast<cudaStream_t>(cuda_stream);
   c->vt = c->opts.prec == SFAIRSC_PREC_FP64 ? VecType::F64 : VecType::F32;
   const int rc = guarded([&] { build_context(c.get(), row_ptr, col_idx, values, group_labels); });
+  if (rc != SFAIRSC_OK) return rc;
+  *out = c.release();
+  return SFAIRSC_OK;
+}
+
+int sfairsc_create_dense(sfairsc_ctx** out, int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
+                         const void* values, int32_t value_dtype, const double* F, int32_t p, int32_t k,
+                         int32_t normalized, const sfairsc_opts* opts, void* cuda_stream) {
+  if (!out) return SFAIRSC_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n < 2 || n > (1ll << 30) || nnz < 1 || nnz > 0x7fffffffll || !row_ptr || !col_idx || !values || p < 0 ||
+      (p > 0 && !F) || k < 1 ||
+      (value_dtype != SFAIRSC_F64 && value_dtype != SFAIRSC_F32 && value_dtype != SFAIRSC_BF16)) {
+    g_last_error = "invalid argument to sfairsc_create_dense";
+    return SFAIRSC_ERR_INVALID_ARG;
+  }
+  if (p + 1 > SFAIRSC_MAX_GROUPS) {
+    g_last_error = "more than 31 constraint columns";
+    return SFAIRSC_ERR_UNSUPPORTED;
+  }
+  std::unique_ptr<sfairsc_ctx> c(new (std::nothrow) sfairsc_ctx());
+  if (!c) return SFAIRSC_ERR_OOM;
+  sfairsc_opts_default(&c->opts);
+  if (opts) c->opts = *opts;
+  if (!valid_opts(c->opts)) {
+    g_last_error = "invalid options";
+    return SFAIRSC_ERR_INVALID_ARG;
+  }
+  c->n = n;
+  c->nnz = nnz;
+  c->h = p + 1;
+  c->k = k;
+  c->normalized = normalized ? 1 : 0;
+  c->vdt_orig = value_dtype;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->vt = c->opts.prec == SFAIRSC_PREC_FP64 ? VecType::F64 : VecType::F32;
+  static const double kNoColumns = 0.0;
+  const int rc = guarded([&] { build_context(c.get(), row_ptr, col_idx, values, nullptr, p > 0 ? F : &kNoColumns); });
   if (rc != SFAIRSC_OK) return rc;
   *out = c.release();
   return SFAIRSC_OK;
@@ -1079,7 +1186,7 @@ int sfairsc_backward(sfairsc_ctx* ctx, const double* grad_lambda, double* grad_v
     }
     const double bw = grad_bandwidth ? bandwidth : 0.0;
     launch_backward((int)ctx->n, ctx->row_ptr, ctx->col, ctx->val_orig, ctx->vdt_orig, k, ctx->Hres, ctx->lam_d, gd, G,
-                    bw, ctx->bw_partial, ctx->bw_blocks, ctx->bw_A, s);
+                    bw, ctx->bw_partial, ctx->bw_blocks, ctx->bw_A, ctx->bw_Hp, ctx->normalized, s);
     if (!od) check_cuda(cudaMemcpyAsync(grad_values, G, sizeof(double) * ctx->nnz, cudaMemcpyDeviceToHost, s), "d2h");
     std::vector<double> part(ctx->bw_blocks);
     check_cuda(cudaMemcpyAsync(part.data(), ctx->bw_partial, sizeof(double) * ctx->bw_blocks, cudaMemcpyDeviceToHost, s),
@@ -1092,6 +1199,165 @@ int sfairsc_backward(sfairsc_ctx* ctx, const double* grad_lambda, double* grad_v
       *grad_bandwidth = bw > 0.0 ? acc : 0.0;
     }
     check_cuda(cudaStreamSynchronize(s), "backward end");
+  });
+}
+
+int sfairsc_backward_vectors(sfairsc_ctx* ctx, const double* grad_H, const double* grad_lambda, double* grad_values,
+                             double bandwidth, double* grad_bandwidth, int32_t max_iter, double rtol,
+                             int32_t* iterations, double* max_rel_resid) {
+  if (!ctx || !grad_H || !grad_values) return SFAIRSC_ERR_INVALID_ARG;
+  if (!ctx->solved) {
+    g_last_error = "sfairsc_backward_vectors needs a prior sfairsc_solve";
+    return SFAIRSC_ERR_INVALID_ARG;
+  }
+  if (ctx->k > 64 || !ctx->normalized) {
+    g_last_error = "the eigenvector-level backward supports the normalized problem with k <= 64";
+    return SFAIRSC_ERR_UNSUPPORTED;
+  }
+  return guarded([&] {
+    cudaStream_t s = ctx->stream;
+    const int n = (int)ctx->n, k = ctx->k;
+    const int iters_max = max_iter > 0 ? max_iter : 1000;
+    const double tol = rtol > 0.0 ? rtol : 1e-10;
+    const std::vector<double>& lam = ctx->lam_h;
+    for (int i = 0; i < k; ++i)
+      for (int j = i + 1; j < k; ++j)
+        if (std::fabs(lam[i] - lam[j]) <= 1e-12 * ctx->sigma)
+          fail(SFAIRSC_ERR_INVALID_ARG, "repeated eigenvalue: its eigenvectors are not differentiable");
+    std::vector<void*> tmp;
+    auto dev = [&](size_t bytes) {
+      void* p = nullptr;
+      check_cuda(cudaMallocAsync(&p, std::max<size_t>(bytes, 8), s), "allocation");
+      tmp.push_back(p);
+      return static_cast<double*>(p);
+    };
+    const size_t nk = (size_t)n * k;
+    const double* G = grad_H;
+    if (!is_device_ptr(grad_H)) {
+      double* d = dev(sizeof(double) * nk);
+      check_cuda(cudaMemcpyAsync(d, grad_H, sizeof(double) * nk, cudaMemcpyHostToDevice, s), "h2d");
+      G = d;
+    }
+    double* glam = nullptr;
+    if (grad_lambda) {
+      glam = dev(sizeof(double) * k);
+      check_cuda(cudaMemcpyAsync(glam, grad_lambda, sizeof(double) * k,
+                                 is_device_ptr(grad_lambda) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s),
+                 "copy");
+    }
+    double *X = dev(8 * nk), *B0 = dev(8 * nk), *Bp = dev(8 * nk), *Zc = dev(8 * nk), *Y = dev(8 * nk),
+           *R = dev(8 * nk), *P = dev(8 * nk), *Q = dev(8 * nk);
+    const int nb = std::max(1, std::min(2 * ctx->sms, (n + 63) / 64));
+    double* part = dev(sizeof(double) * nb * k * k);
+    double* small = dev(sizeof(double) * (3 * k + k * k));  // alpha / beta / ones, k x k coefficients
+    std::vector<double> hpart((size_t)nb * k * k);
+    auto gram = [&](const double* A, const double* Bm) {  // A^T Bm (k x k, [i][j] = A_i . Bm_j), summed in block order
+      launch_col_gram(n, k, A, k, Bm, part, nb, s);
+      check_cuda(cudaMemcpyAsync(hpart.data(), part, sizeof(double) * nb * k * k, cudaMemcpyDeviceToHost, s), "d2h");
+      check_cuda(cudaStreamSynchronize(s), "gram");
+      std::vector<double> T((size_t)k * k, 0.0);
+      for (int b = 0; b < nb; ++b)
+        for (int q = 0; q < k * k; ++q) T[q] += hpart[(size_t)b * k * k + q];
+      return T;
+    };
+    auto dots = [&](const double* A, const double* Bm) {
+      launch_col_dots(n, k, A, Bm, part, nb, s);
+      check_cuda(cudaMemcpyAsync(hpart.data(), part, sizeof(double) * nb * k, cudaMemcpyDeviceToHost, s), "d2h");
+      check_cuda(cudaStreamSynchronize(s), "dots");
+      std::vector<double> d(k, 0.0);
+      for (int b = 0; b < nb; ++b)
+        for (int i = 0; i < k; ++i) d[i] += hpart[(size_t)b * k + i];
+      return d;
+    };
+    auto upload = [&](const std::vector<double>& v, double* dst) {
+      check_cuda(cudaMemcpyAsync(dst, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice, s), "h2d");
+    };
+    auto right_mul = [&](const double* A, const std::vector<double>& C, double beta, double* out) {
+      std::vector<double> Cc(C);
+      upload(Cc, small + 3 * k);
+      launch_col_gemm(n, k, A, k, small + 3 * k, beta, out, s);
+      check_cuda(cudaStreamSynchronize(s), "right product");  // the coefficient slot is reused next
+    };
+    // X = D^{1/2} H (unit columns, the returned signs); B0 = D^{-1/2} Gbar; Bp = P B0
+    launch_rows_to_cols_scaled(n, k, ctx->Hres, ctx->dinv64, 1, X, s);
+    launch_rows_to_cols_scaled(n, k, G, ctx->dinv64, 0, B0, s);
+    launch_operator(ctx->proj64, VecType::F64, B0, 1, n, Bp, 1, n, k, s);
+    // the computed eigenvectors' part: z_i = sum_{j != i} x_j (x_j^T b_i) / (lambda_i - lambda_j)
+    std::vector<double> T = gram(X, Bp);  // T[j][i] = x_j . b_i
+    std::vector<double> Ck((size_t)k * k, 0.0), mT((size_t)k * k);
+    for (int j = 0; j < k; ++j)
+      for (int i = 0; i < k; ++i) {
+        if (i != j) Ck[(size_t)j * k + i] = T[(size_t)j * k + i] / (lam[i] - lam[j]);
+        mT[(size_t)j * k + i] = -T[(size_t)j * k + i];
+      }
+    right_mul(X, Ck, 0.0, Zc);
+    // the rest: (A - lambda_i) y_i = (I - X X^T) b_i on the complement, where it is positive definite
+    check_cuda(cudaMemcpyAsync(R, Bp, 8 * nk, cudaMemcpyDeviceToDevice, s), "copy");
+    right_mul(X, mT, 1.0, R);
+    check_cuda(cudaMemsetAsync(Y, 0, 8 * nk, s), "memset");
+    check_cuda(cudaMemcpyAsync(P, R, 8 * nk, cudaMemcpyDeviceToDevice, s), "copy");
+    std::vector<double> rho = dots(R, R), bnorm(k), coef(k);
+    for (int i = 0; i < k; ++i) bnorm[i] = std::sqrt(rho[i]);
+    upload(lam, small + 2 * k);  // the shifts
+    std::vector<char> done(k, 0);
+    int it = 0;
+    double worst = 0.0;
+    for (; it < iters_max; ++it) {
+      worst = 0.0;
+      bool all = true;
+      for (int i = 0; i < k; ++i) {
+        const double rr = bnorm[i] > 0.0 ? std::sqrt(rho[i]) / bnorm[i] : 0.0;
+        done[i] = rr <= tol;
+        worst = std::max(worst, rr);
+        all = all && done[i];
+      }
+      if (all) break;
+      apply_op(ctx, true, P, 1, n, Q, 1, n, k);
+      launch_col_shift(n, k, Q, P, small + 2 * k, s);
+      std::vector<double> Tq = gram(X, Q);
+      for (double& v : Tq) v = -v;
+      right_mul(X, Tq, 1.0, Q);
+      std::vector<double> pq = dots(P, Q);
+      for (int i = 0; i < k; ++i) coef[i] = (done[i] || !(pq[i] > 0.0)) ? 0.0 : rho[i] / pq[i];
+      upload(coef, small);
+      launch_cg_update(n, k, Y, R, P, Q, small, s);
+      std::vector<double> rn = dots(R, R);
+      for (int i = 0; i < k; ++i) {
+        coef[i] = done[i] || rho[i] == 0.0 ? 0.0 : rn[i] / rho[i];
+        rho[i] = rn[i];
+      }
+      upload(coef, small + k);
+      launch_cg_direction(n, k, P, R, small + k, s);
+    }
+    check_err_word(ctx);
+    // z_i = known part - y_i; c_i = gbar_i . h_i = b0_i . x_i
+    std::vector<double> ones(k, 1.0);
+    upload(ones, small);
+    launch_col_shift(n, k, Zc, Y, small, s);
+    std::vector<double> cvec = dots(B0, X);
+    upload(cvec, small + k);
+    const int kp = (2 * k + 3) / 4 * 4;
+    double *A = dev(8 * (size_t)n), *Qp = dev(8 * (size_t)n * kp), *Gp = dev(8 * (size_t)n * kp);
+    launch_vector_vertex(n, k, kp, ctx->Hres, Zc, ctx->dinv64, ctx->lam_d, glam, small + k, A, Qp, Gp, s);
+    const bool od = is_device_ptr(grad_values);
+    double* gout = od ? grad_values : dev(8 * (size_t)ctx->nnz);
+    const double bw = grad_bandwidth ? bandwidth : 0.0;
+    launch_sddmm_rows(n, ctx->row_ptr, ctx->col, ctx->val_orig, ctx->vdt_orig, kp, Qp, Gp, A, gout, bw,
+                      ctx->bw_partial, ctx->bw_blocks, s);
+    if (!od) check_cuda(cudaMemcpyAsync(grad_values, gout, 8 * (size_t)ctx->nnz, cudaMemcpyDeviceToHost, s), "d2h");
+    std::vector<double> bp(ctx->bw_blocks);
+    check_cuda(cudaMemcpyAsync(bp.data(), ctx->bw_partial, sizeof(double) * bp.size(), cudaMemcpyDeviceToHost, s),
+               "d2h");
+    check_cuda(cudaStreamSynchronize(s), "vector backward");
+    for (void* p : tmp) cudaFreeAsync(p, s);
+    check_cuda(cudaStreamSynchronize(s), "vector backward free");
+    if (grad_bandwidth) {
+      double acc = 0.0;
+      for (double v : bp) acc += v;
+      *grad_bandwidth = bw > 0.0 ? acc : 0.0;
+    }
+    if (iterations) *iterations = it;
+    if (max_rel_resid) *max_rel_resid = worst;
   });
 }
 

@@ -83,6 +83,7 @@ struct OpPlan {
   unsigned long long wait_ns = 2000000000ull;  // bound of every device-side wait
   const unsigned* stall_flag = nullptr;  // non-null: the launch first waits for this word (never set) to become nonzero
   WindowTable win[3];  // by block size b = 1, 2, 4 (index 0, 1, 2)
+  const void* Fd = nullptr;  // dense constraints F (n x (h - 1), row-major, vector type) instead of labels
 };
 
 // Rows of ytil (b values of vs bytes) a window may hold next to the kernel's other shared memory.
@@ -113,6 +114,13 @@ void launch_sigma_rows(int n, const int32_t* row_ptr, const int32_t* col, const 
                        const double* dinv64, const double* deg, int normalized, double* blockmax, int nblocks,
                        cudaStream_t s);
 void launch_row_partition(int n, const int32_t* row_ptr, int grid, int row_weight, int32_t* cta_rows, cudaStream_t s);
+// Dense constraint matrix F (n x p row-major FP64): per-block partial sums of C^T C (p x p) and of
+// F^T H (p x k, H n x k row-major); an FP64 -> FP32 copy.
+void launch_dense_ctc(int n, int p, const double* F, const double* deg, int normalized, double* partial, int nblocks,
+                      cudaStream_t s);
+void launch_dense_fth(int n, int p, int k, const double* F, const double* H, double* partial, int nblocks,
+                      cudaStream_t s);
+void launch_f64_to_f32(int64_t count, const double* in, float* out, cudaStream_t s);
 
 // Krylov kernels.
 struct OrthPlan {
@@ -172,10 +180,30 @@ void launch_diagnostics(int n, int k, int h, const double* H, const double* deg,
                         const double* params, double* partial, int nblocks, double* out, cudaStream_t s, bool fp64);
 
 // Backward SDDMM.
-// grad[e] for every stored entry; partial[b] = per-block sum of the bandwidth terms; A = n-vector workspace.
+// grad[e] for every stored entry; partial[b] = per-block sum of the bandwidth terms; A = n-vector
+// workspace; Hp = n x backward_padded_width(k) workspace (H with rows padded to a multiple of 4).
+int backward_padded_width(int k);
 void launch_backward(int n, const int32_t* row_ptr, const int32_t* col, const void* val, int val_dtype, int k,
                      const double* H, const double* lam, const double* gbar, double* grad, double bandwidth,
-                     double* partial, int nblocks, double* A, cudaStream_t s);
+                     double* partial, int nblocks, double* A, double* Hp, int normalized, cudaStream_t s);
+
+void launch_sddmm_rows(int n, const int32_t* row_ptr, const int32_t* col, const void* val, int val_dtype, int kp,
+                       const double* Qp, const double* Gp, const double* A, double* grad, double bandwidth,
+                       double* partial, int nblocks, cudaStream_t s);
+// Eigenvector-level backward helpers (column-major n x k blocks, FP64).
+void launch_rows_to_cols_scaled(int n, int k, const double* G, const double* s, int divide, double* out,
+                                cudaStream_t st);
+void launch_col_gram(int n, int k1, const double* X, int k2, const double* Y, double* partial, int nblocks,
+                     cudaStream_t s);
+void launch_col_gemm(int n, int k1, const double* X, int k2, const double* C, double beta, double* out, cudaStream_t s);
+void launch_col_dots(int n, int k, const double* A, const double* B, double* partial, int nblocks, cudaStream_t s);
+void launch_col_shift(int n, int k, double* Q, const double* P, const double* shift, cudaStream_t s);
+void launch_cg_update(int n, int k, double* Y, double* R, const double* P, const double* Q, const double* alpha,
+                      cudaStream_t s);
+void launch_cg_direction(int n, int k, double* P, const double* R, const double* beta, cudaStream_t s);
+void launch_vector_vertex(int n, int k, int kp, const double* H, const double* Zc, const double* dinv,
+                          const double* lam, const double* glam, const double* cvec, double* A, double* Qp, double* Gp,
+                          cudaStream_t s);
 
 // k-means (device part).  Returns inertia and iterations of the winner.
 struct KmeansResult {

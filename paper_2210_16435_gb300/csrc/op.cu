@@ -52,6 +52,9 @@ struct OpArgs {
   const int32_t* __restrict__ cta_seg;
   int win_rows;
   int win_off;  // byte offset of the window in dynamic shared memory
+  // dense constraints: F (n x fp, row-major, in the vector type) replaces the group labels
+  const VT* __restrict__ Fd;
+  int fp;
 };
 
 template <typename VT, int B>
@@ -137,16 +140,17 @@ __device__ __forceinline__ void reduce_partials(const double* partial, int nctas
 // Also returns a itself (for the shift term).  Threads v < B work.
 template <int B>
 __device__ __forceinline__ void solve_groups(const double* tot, const double* params, int h, double* a_out,
-                                             double* coef) {
+                                             double* coef, bool dense = false) {
   const int v = threadIdx.x;
   if (v < B) {
     const int p = h - 1;
     double sum = 0.0;
-    for (int s = 0; s < h; ++s) sum += tot[s * B + v];
+    if (!dense)
+      for (int s = 0; s < h; ++s) sum += tot[s * B + v];
     double y[kMaxGroups];
-    // forward: L y = rhs, rhs_s = tot_s - z_s * sum
+    // forward: L y = rhs, rhs_s = tot_s - z_s * sum (labels) or tot_s (dense F: tot = C^T x)
     for (int s = 0; s < p; ++s) {
-      double r = tot[s * B + v] - params[kPZ + s] * sum;
+      double r = tot[s * B + v] - (dense ? 0.0 : params[kPZ + s] * sum);
       for (int q = 0; q < s; ++q) r -= params[kPL + s * kLStride + q] * y[q];
       y[s] = r * params[kPLinv + s];
     }
@@ -157,10 +161,11 @@ __device__ __forceinline__ void solve_groups(const double* tot, const double* pa
       y[s] = r * params[kPLinv + s];
     }
     double za = 0.0;
-    for (int s = 0; s < p; ++s) za += params[kPZ + s] * y[s];
+    if (!dense)
+      for (int s = 0; s < p; ++s) za += params[kPZ + s] * y[s];
     for (int s = 0; s < p; ++s) {
       a_out[s * B + v] = y[s];
-      coef[s * B + v] = y[s] - za;
+      coef[s * B + v] = y[s] - za;  // labels: (C a)_i = d_i^{-1/2} coef[g_i]; dense: coef = a
     }
     coef[p * B + v] = -za;
   }
@@ -277,6 +282,99 @@ __device__ void cta_group_sums(int r0, int r1, int h, const uint8_t* __restrict_
   __syncthreads();
 }
 
+// Dense-constraint sums C^T x over rows [r0, r1) of this CTA (C = D^{-1/2} F,
+// the scaling folded into f): partial[blockIdx.x][s * B + v] = sum_r F[r][s] f(r)_v
+// for s < p, zero in the slot s = p.  Thread per row, four columns per pass;
+// the same FP32 windows and TwoSum carries as the group sums, fixed order.
+template <typename VT, int B, typename Fn>
+__device__ void cta_dense_sums(int r0, int r1, int p, const VT* __restrict__ Fd, double* red, double* partial, Fn&& f) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int h = p + 1, P = h * B;
+  for (int s0 = 0; s0 < p; s0 += 4) {
+    if constexpr (sizeof(VT) == 4) {
+      float win[4][B];
+      Comp32 acc[4][B];
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int v = 0; v < B; ++v) {
+          win[j][v] = 0.f;
+          acc[j][v].zero();
+        }
+      int cnt = 0;
+      for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        float x[B], fr[4];
+        f(r, x);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) fr[j] = s0 + j < p ? Fd[(size_t)r * p + s0 + j] : 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+          for (int v = 0; v < B; ++v) win[j][v] = fmaf(fr[j], x[v], win[j][v]);
+        if (++cnt == 8) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int v = 0; v < B; ++v) {
+              acc[j][v].add(win[j][v]);
+              win[j][v] = 0.f;
+            }
+          cnt = 0;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int v = 0; v < B; ++v) {
+          acc[j][v].add(win[j][v]);
+          acc[j][v].reduce(1);
+        }
+      if (lane == 0)
+        for (int j = 0; j < 4 && s0 + j < p; ++j)
+#pragma unroll
+          for (int v = 0; v < B; ++v) red[warp * P + (s0 + j) * B + v] = acc[j][v].slot();
+    } else {
+      double acc[4][B];
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int v = 0; v < B; ++v) acc[j][v] = 0.0;
+      for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        double x[B];
+        f(r, x);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const double fr = s0 + j < p ? (double)Fd[(size_t)r * p + s0 + j] : 0.0;
+#pragma unroll
+          for (int v = 0; v < B; ++v) acc[j][v] = fma(fr, x[v], acc[j][v]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int v = 0; v < B; ++v) acc[j][v] = warp_allsum(acc[j][v]);
+      if (lane == 0)
+        for (int j = 0; j < 4 && s0 + j < p; ++j)
+#pragma unroll
+          for (int v = 0; v < B; ++v) red[warp * P + (s0 + j) * B + v] = acc[j][v];
+    }
+  }
+  if (lane == 0)
+#pragma unroll
+    for (int v = 0; v < B; ++v) red[warp * P + p * B + v] = 0.0;  // a zero (sum, carry) pair packs to 0.0 too
+  __syncthreads();
+  for (int q = threadIdx.x; q < P; q += blockDim.x) {
+    double sum = 0.0;
+    if constexpr (sizeof(VT) == 4) {
+      sum = comp32_slot_sum(red + q, nwarps, P);
+    } else {
+      for (int wv = 0; wv < nwarps; ++wv) sum += red[wv * P + q];
+    }
+    partial[(size_t)blockIdx.x * P + q] = sum;
+  }
+  __syncthreads();
+}
+
 template <typename VT, typename MT, int B>
 __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -297,10 +395,32 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
   if (a.stall && !wait_flag(a.stall, a.err, a.wait_ns)) return;
 
   auto scale = [&](int r) -> VT { return a.normalized ? a.dinv[r] : VT(1); };
+  const bool dense = a.Fd != nullptr;
+  // (C coef)_r / d_r^{-1/2} for the B vectors: the group's entry, or F's row times coef (dense)
+  auto corr = [&](int r, const VT* cv, VT (&c)[B]) {
+    if (dense) {
+#pragma unroll
+      for (int v = 0; v < B; ++v) c[v] = VT(0);
+      const VT* fr = a.Fd + (size_t)r * a.fp;
+      for (int s2 = 0; s2 < a.fp; ++s2) {
+        const VT f = fr[s2];
+#pragma unroll
+        for (int v = 0; v < B; ++v) c[v] = fma(f, cv[s2 * B + v], c[v]);
+      }
+    } else {
+      const int g = a.lab[r];
+#pragma unroll
+      for (int v = 0; v < B; ++v) c[v] = cv[g * B + v];
+    }
+  };
+  auto group_sums = [&](auto&& f) {
+    if (dense) cta_dense_sums<VT, B>(r0, r1, a.fp, a.Fd, red, a.partial, f);
+    else cta_group_sums<VT, B>(r0, r1, h, a.lab, red, a.partial, f);
+  };
 
   // ---------------- phase A: group sums of D^{-1/2} w over own rows
   if (grouped) {
-    cta_group_sums<VT, B>(r0, r1, h, a.lab, red, a.partial, [&](int r, VT(&x)[B]) {
+    group_sums([&](int r, VT(&x)[B]) {
       const VT sc = scale(r);
       load_strided<VT, B>(a.w, r, a.wrs, a.wcs, x);
 #pragma unroll
@@ -309,7 +429,7 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
     if (!grid_sync(a.bar, a.err, a.wait_ns)) return;
     // ---------------- phase B: a = (C^T C)^{-1} C^T w
     reduce_partials(a.partial, gridDim.x, P, scratch, tot);
-    solve_groups<B>(tot, a.params, h, avec, coefA);
+    solve_groups<B>(tot, a.params, h, avec, coefA, dense);
   } else {
     for (int i = threadIdx.x; i < kMaxGroups * B; i += blockDim.x) {
       coefA[i] = 0.0;
@@ -321,26 +441,151 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
   __syncthreads();
   if (a.mode == 1) {  // P w only
     for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-      const int g = a.lab[r];
       const VT sc = scale(r);
+      VT cr[B];
+      corr(r, coefAv, cr);
 #pragma unroll
-      for (int v = 0; v < B; ++v) a.out[r * a.ors + v * a.ocs] = a.w[r * a.wrs + v * a.wcs] - sc * coefAv[g * B + v];
+      for (int v = 0; v < B; ++v) a.out[r * a.ors + v * a.ocs] = a.w[r * a.wrs + v * a.wcs] - sc * cr[v];
     }
     return;
   }
 #pragma unroll 4
   for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-    const int g = a.lab[r];
     const VT sc = scale(r);
+    VT cr[B];
+    corr(r, coefAv, cr);
 #pragma unroll
     for (int v = 0; v < B; ++v) {
-      const VT y = a.w[r * a.wrs + v * a.wcs] - sc * coefAv[g * B + v];
+      const VT y = a.w[r * a.wrs + v * a.wcs] - sc * cr[v];
       a.ytil[(size_t)r * B + v] = a.normalized ? sc * y : y;
     }
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.work = 0u;  // no CTA takes a row block before the barrier
   if (!grid_sync(a.bar, a.err, a.wait_ns)) return;
 
-  // ---------------- phase C: t = L_n y over this CTA's rows, written to out
+  // ---------------- phase C (no windows): t = L_n y, written to out
+  // Warps take blocks of 4 row groups from a global counter (load balance
+  // across CTAs); Lr lanes per row, each holding up to U (column, weight)
+  // pairs of its row per pass; within a block the pairs of the next row group
+  // and the bounds of the group after it are loaded while this group's ytil
+  // rows are gathered.  Sums per row by a fixed shuffle tree (reproducible).
+  if (!a.seg_row) {
+    constexpr int U = sizeof(VT) == 4 ? 8 : 4;
+    constexpr int kGroupsPerBlock = 4;
+    const int Lr = a.lanes;
+    const int sub = lane & (Lr - 1);
+    const int rpw = 32 / Lr;
+    const int n = a.n;
+    auto bounds = [&](int rb, int rend, int& e, int& e1) {
+      const int r = rb + lane / Lr;
+      if (r < rend) {
+        e = __ldg(a.row_ptr + r) + sub;
+        e1 = __ldg(a.row_ptr + r + 1);
+      } else {
+        e = 0;
+        e1 = 0;
+      }
+    };
+    auto fetch = [&](int e, int e1, int (&c)[U], VT (&wv)[U]) {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int ee = e + u * Lr;
+        const bool in = ee < e1;
+        c[u] = in ? __ldg(a.col + ee) : -1;
+        wv[u] = in ? val_as<VT>(a.val[ee]) : VT(0);
+      }
+    };
+    const int blk_rows = rpw * kGroupsPerBlock;
+    const int nblocks = (n + blk_rows - 1) / blk_rows;
+    auto grab = [&]() {
+      int b = 0;
+      if (lane == 0) b = (int)atomicAdd(a.work, 1u);
+      return __shfl_sync(0xffffffffu, b, 0);
+    };
+    // look-ahead iterator over the row groups of the blocks this warp takes
+    // (row base n = exhausted); the block after the current one is taken early
+    int la_blk = grab(), la_next = grab();
+    int la_rb = la_blk < nblocks ? la_blk * blk_rows : n;
+    auto advance = [&]() {
+      if (la_rb >= n) return;
+      la_rb += rpw;
+      if (la_rb >= min(n, la_blk * blk_rows + blk_rows)) {
+        la_blk = la_next;
+        la_rb = la_blk < nblocks ? la_blk * blk_rows : n;
+        if (la_blk < nblocks) la_next = grab();
+      }
+    };
+    auto rend_of = [&](int rb) { return min(n, (rb / blk_rows) * blk_rows + blk_rows); };
+    int rb_cur = la_rb;
+    advance();
+    int rb_nx = la_rb;
+    advance();
+    int e_cur, e1_cur, e_nx, e1_nx;
+    int c_cur[U];
+    VT w_cur[U];
+    bounds(rb_cur, rb_cur < n ? rend_of(rb_cur) : n, e_cur, e1_cur);
+    fetch(e_cur, e1_cur, c_cur, w_cur);
+    bounds(rb_nx, rb_nx < n ? rend_of(rb_nx) : n, e_nx, e1_nx);
+    while (rb_cur < n) {
+      int c_nx[U];
+      VT w_nx[U];
+      fetch(e_nx, e1_nx, c_nx, w_nx);  // the next group's pairs, in flight during this group's gathers
+      const int rb_nn = la_rb;
+      advance();
+      int e_nn, e1_nn;
+      bounds(rb_nn, rb_nn < n ? rend_of(rb_nn) : n, e_nn, e1_nn);
+      const int rend = rend_of(rb_cur);
+      VT sacc[B];
+#pragma unroll
+      for (int v = 0; v < B; ++v) sacc[v] = VT(0);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (c_cur[u] >= 0) {
+          VT y[B];
+          load_row<VT, B>(a.ytil + (size_t)c_cur[u] * B, y);
+#pragma unroll
+          for (int v = 0; v < B; ++v) sacc[v] = fma(w_cur[u], y[v], sacc[v]);
+        }
+      }
+      for (int e = e_cur + U * Lr; e < e1_cur; e += Lr) {  // rows longer than U * Lr entries
+        const int c = __ldg(a.col + e);
+        const VT w = val_as<VT>(a.val[e]);
+        VT y[B];
+        load_row<VT, B>(a.ytil + (size_t)c * B, y);
+#pragma unroll
+        for (int v = 0; v < B; ++v) sacc[v] = fma(w, y[v], sacc[v]);
+      }
+      for (int o = Lr >> 1; o > 0; o >>= 1)
+#pragma unroll
+        for (int v = 0; v < B; ++v) sacc[v] += __shfl_xor_sync(0xffffffffu, sacc[v], o);
+      const int r = rb_cur + lane / Lr;
+      if (r < rend && sub == 0) {
+        const VT sc = scale(r);
+        VT dd = VT(1);
+        if (!a.normalized) dd = (VT)a.deg[r];
+        VT wr[B], cr[B];
+        load_strided<VT, B>(a.w, r, a.wrs, a.wcs, wr);
+        corr(r, coefAv, cr);
+#pragma unroll
+        for (int v = 0; v < B; ++v) {
+          const VT y = wr[v] - sc * cr[v];
+          a.out[r * a.ors + v * a.ocs] = a.normalized ? y - sc * sacc[v] : dd * y - sacc[v];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        c_cur[u] = c_nx[u];
+        w_cur[u] = w_nx[u];
+      }
+      e_cur = e_nx;
+      e1_cur = e1_nx;
+      e_nx = e_nn;
+      e1_nx = e1_nn;
+      rb_cur = rb_nx;
+      rb_nx = rb_nn;
+    }
+  }
+  // ---------------- phase C (windows): t = L_n y over this CTA's rows, written to out
   // The CTA's rows come as segments; a segment with a window first stages
   // ytil rows [ws, ws + win_rows) in shared memory, and each gather reads
   // from there when its column falls inside, from L2 otherwise (one generic
@@ -348,7 +593,7 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
   // lanes per row each hold up to U (column, weight) pairs of the row per
   // pass, and the next group's pairs are loaded while this group's ytil rows
   // are gathered.  Sums per row by a fixed shuffle tree (reproducible).
-  {
+  if (a.seg_row) {
     constexpr int U = sizeof(VT) == 4 ? 8 : 4;
     const int Lr = a.lanes;
     const int sub = lane & (Lr - 1);
@@ -356,8 +601,8 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
     const int n = a.n;
     const int warp = threadIdx.x >> 5;
     VT* win = reinterpret_cast<VT*>(smem_raw + a.win_off);
-    const int sg0 = a.seg_row ? a.cta_seg[blockIdx.x] : 0;
-    const int sg1 = a.seg_row ? a.cta_seg[blockIdx.x + 1] : 1;
+    const int sg0 = a.cta_seg[blockIdx.x];
+    const int sg1 = a.cta_seg[blockIdx.x + 1];
     auto fetch = [&](int e, int e1, int (&c)[U], VT (&wv)[U]) {
 #pragma unroll
       for (int u = 0; u < U; ++u) {
@@ -368,9 +613,9 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
       }
     };
     for (int sg = sg0; sg < sg1; ++sg) {
-      const int rs = a.seg_row ? a.seg_row[sg] : r0;
-      const int re = a.seg_row ? a.seg_row[sg + 1] : r1;
-      const int ws = a.seg_row ? a.seg_ws[sg] : -1;
+      const int rs = a.seg_row[sg];
+      const int re = a.seg_row[sg + 1];
+      const int ws = a.seg_ws[sg];
       int wlen = 0;
       if (ws >= 0) {
         wlen = min(a.win_rows, n - ws);
@@ -439,15 +684,15 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
           for (int v = 0; v < B; ++v) sacc[v] += __shfl_xor_sync(0xffffffffu, sacc[v], o);
         const int r = rs + q * rpw + lane / Lr;
         if (r < re && sub == 0) {
-          const int g = a.lab[r];
           const VT sc = scale(r);
           VT dd = VT(1);
           if (!a.normalized) dd = (VT)a.deg[r];
-          VT wr[B];
+          VT wr[B], cr[B];
           load_strided<VT, B>(a.w, r, a.wrs, a.wcs, wr);
+          corr(r, coefAv, cr);
 #pragma unroll
           for (int v = 0; v < B; ++v) {
-            const VT y = wr[v] - sc * coefAv[g * B + v];
+            const VT y = wr[v] - sc * cr[v];
             a.out[r * a.ors + v * a.ocs] = a.normalized ? y - sc * sacc[v] : dd * y - sacc[v];
           }
         }
@@ -466,7 +711,7 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
   if (!grouped) return;
   // t rows were written by any CTA: make them visible, then group sums over own rows (through L2)
   if (!grid_sync(a.bar, a.err, a.wait_ns)) return;
-  cta_group_sums<VT, B>(r0, r1, h, a.lab, red, a.partial, [&](int r, VT(&x)[B]) {
+  group_sums([&](int r, VT(&x)[B]) {
     const VT sc = scale(r);
     if (a.ocs == 1 && a.ors == B) {
       load_row_cg<VT, B>(a.out + (size_t)r * B, x);
@@ -484,7 +729,7 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
   {
     // reuse solve_groups on tot, then fold in -sigma a
     double* bvec = scratch;  // scratch is free now (reduce_partials synced)
-    solve_groups<B>(tot, a.params, h, bvec, coefD);
+    solve_groups<B>(tot, a.params, h, bvec, coefD, dense);
     const double sigma = a.params[kPSigma];
     if (threadIdx.x < B) {
       const int v = threadIdx.x;
@@ -492,7 +737,7 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
       double zu = 0.0;
       for (int s = 0; s < p; ++s) {
         const double u = bvec[s * B + v] - sigma * avec[s * B + v];
-        zu += a.params[kPZ + s] * u;
+        if (!dense) zu += a.params[kPZ + s] * u;
         coefD[s * B + v] = u;
       }
       for (int s = 0; s < p; ++s) coefD[s * B + v] -= zu;
@@ -504,12 +749,13 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
   }
 #pragma unroll 4
   for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-    const int g = a.lab[r];
     const VT sc = scale(r);
+    VT cr[B];
+    corr(r, coefAv, cr);
 #pragma unroll
     for (int v = 0; v < B; ++v) {
       VT* o = a.out + r * a.ors + v * a.ocs;
-      *o = __ldcg(o) - sc * coefAv[g * B + v];
+      *o = __ldcg(o) - sc * cr[v];
     }
   }
 }
@@ -560,6 +806,8 @@ static void launch_t(const OpPlan& p, const void* w, int64_t wrs, int64_t wcs, v
   a.cta_seg = windows ? wt.cta_seg : nullptr;
   a.win_rows = windows ? wt.win_rows : 0;
   a.win_off = (int)((base + 15) / 16 * 16);
+  a.Fd = static_cast<const VT*>(p.Fd);
+  a.fp = p.Fd ? p.h - 1 : 0;
   const size_t smem = (size_t)a.win_off + (windows ? (size_t)wt.win_rows * B * sizeof(VT) : 0);
   auto kern = fused_operator_kernel<VT, MT, B>;
   check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "operator smem attr");

@@ -224,3 +224,83 @@ void launch_row_partition(int n, const int32_t* row_ptr, int grid, int row_weigh
 }
 
 }  // namespace sfairsc
+
+namespace sfairsc {
+
+// C^T C for a dense constraint matrix (C = D^{-1/2} F, or F for the unnormalized extension):
+// partial[b][s * p + t] = sum over block b's rows of F_rs F_rt / d_r.  Rows are staged 64 at a
+// time (scaled by d_r^{-1/2}); thread q owns the entries q, q + 256, ... (p * p <= 961).
+__global__ void dense_ctc_kernel(int n, int p, const double* __restrict__ F, const double* __restrict__ deg,
+                                 int normalized, double* partial) {
+  extern __shared__ double tile[];  // 64 x p
+  const int npair = p * p;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int t0 = blockIdx.x * 64; t0 < n; t0 += gridDim.x * 64) {
+    const int rows = min(64, n - t0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < 64 * p; e += blockDim.x) {
+      const int rr = e / p, s = e % p;
+      double v = 0.0;
+      if (rr < rows) {
+        const int r = t0 + rr;
+        v = F[(size_t)r * p + s];
+        if (normalized) v /= sqrt(deg[r]);
+      }
+      tile[e] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int q = threadIdx.x + j * blockDim.x;
+      if (q < npair) {
+        const int s = q / p, t = q % p;
+        double sacc = 0.0;
+        for (int rr = 0; rr < rows; ++rr) sacc = fma(tile[rr * p + s], tile[rr * p + t], sacc);
+        acc[j] += sacc;
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int q = threadIdx.x + j * blockDim.x;
+    if (q < npair) partial[(size_t)blockIdx.x * npair + q] = acc[j];
+  }
+}
+
+void launch_dense_ctc(int n, int p, const double* F, const double* deg, int normalized, double* partial, int nblocks,
+                      cudaStream_t s) {
+  dense_ctc_kernel<<<nblocks, 256, sizeof(double) * 64 * p, s>>>(n, p, F, deg, normalized, partial);
+  check_cuda(cudaGetLastError(), "dense C^T C launch");
+}
+
+// partial[b][s * k + i] = sum over block b's rows of F_rs H_ri (F^T H, the fairness residual of a
+// dense constraint matrix); thread q owns the entries q, q + 256, ...
+__global__ void dense_fth_kernel(int n, int p, int k, const double* __restrict__ F, const double* __restrict__ H,
+                                 double* partial) {
+  const int per = (n + gridDim.x - 1) / gridDim.x;
+  const int r0 = blockIdx.x * per, r1 = min(n, r0 + per);
+  for (int q = threadIdx.x; q < p * k; q += blockDim.x) {
+    const int s = q / k, i = q % k;
+    double acc = 0.0;
+    for (int r = r0; r < r1; ++r) acc = fma(F[(size_t)r * p + s], H[(size_t)r * k + i], acc);
+    partial[(size_t)blockIdx.x * p * k + q] = acc;
+  }
+}
+
+void launch_dense_fth(int n, int p, int k, const double* F, const double* H, double* partial, int nblocks,
+                      cudaStream_t s) {
+  dense_fth_kernel<<<nblocks, 256, 0, s>>>(n, p, k, F, H, partial);
+  check_cuda(cudaGetLastError(), "dense F^T H launch");
+}
+
+__global__ void f64_to_f32_rows_kernel(int64_t count, const double* in, float* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
+void launch_f64_to_f32(int64_t count, const double* in, float* out, cudaStream_t s) {
+  f64_to_f32_rows_kernel<<<1024, 256, 0, s>>>(count, in, out);
+  check_cuda(cudaGetLastError(), "conversion launch");
+}
+
+}  // namespace sfairsc

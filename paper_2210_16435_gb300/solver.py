@@ -22,6 +22,8 @@ class FairSC:
     row_ptr, col_idx: int32 CSR of the symmetric weight matrix W (both triangles);
     values: float64 / float32 / bfloat16 weights; groups: int32 labels in [0, h).
     Tensors may live on the GPU (borrowed: keep them alive) or the CPU (copied).
+    F: a dense float64 constraint matrix (n x p) in place of the groups (pass groups=None);
+    the constraint is then F^T H = 0 (sfairsc_create_dense).
     """
 
     def __init__(self, row_ptr, col_idx, values, groups, k: int, h: int | None = None, normalized: bool = True,
@@ -29,9 +31,14 @@ class FairSC:
                  sigma: float | None = None, seed: int = 1, kmeans_seed: int = 0, kmeans_n_init: int = 1,
                  kmeans_max_iter: int = 100, validate: int = 1, profile: int = 0, wait_limit_us: int = 0,
                  fault_inject: int = 0, spmv_window: int = 0, orth_mode: int = 0,
-                 stream: torch.cuda.Stream | None = None):
+                 stream: torch.cuda.Stream | None = None, F: torch.Tensor | None = None):
+        if F is not None:
+            F = F.to(torch.float64).contiguous()
+            groups = torch.zeros(row_ptr.numel() - 1, dtype=torch.int32, device=row_ptr.device)
         self._keep = [t.contiguous() for t in (row_ptr, col_idx, values, groups)]
         row_ptr, col_idx, values, groups = self._keep
+        if F is not None:
+            self._keep.append(F)
         if row_ptr.dtype != torch.int32 or col_idx.dtype != torch.int32 or groups.dtype != torch.int32:
             raise TypeError("row_ptr, col_idx and groups must be int32")
         if values.dtype not in _DTYPES:
@@ -39,16 +46,24 @@ class FairSC:
         self.n = row_ptr.numel() - 1
         self.nnz = col_idx.numel()
         self.k = int(k)
-        self.h = int(h) if h is not None else int(groups.max().item()) + 1
+        if F is not None:
+            self.h = F.shape[1] + 1
+        else:
+            self.h = int(h) if h is not None else int(groups.max().item()) + 1
         self.prec = prec
         self.vec_dtype = torch.float64 if prec == "fp64" else torch.float32
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         opts = B.make_opts(prec, block, tol, basis, max_restarts, sigma, seed, kmeans_seed, kmeans_n_init,
                            kmeans_max_iter, validate, profile, wait_limit_us, fault_inject, spmv_window, orth_mode)
-        self.ctx = B.sfairsc_create(self.n, self.nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(values), _DTYPES[values.dtype],
-                                    _ptr(groups), self.h, self.k, 1 if normalized else 0, opts,
-                                    self.stream.cuda_stream)
+        if F is not None:
+            self.ctx = B.sfairsc_create_dense(self.n, self.nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(values),
+                                              _DTYPES[values.dtype], _ptr(F), F.shape[1], self.k,
+                                              1 if normalized else 0, opts, self.stream.cuda_stream)
+        else:
+            self.ctx = B.sfairsc_create(self.n, self.nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(values),
+                                        _DTYPES[values.dtype], _ptr(groups), self.h, self.k, 1 if normalized else 0,
+                                        opts, self.stream.cuda_stream)
         self.sigma = B.sfairsc_get_sigma(self.ctx)
         self.info = None
 
@@ -88,6 +103,17 @@ class FairSC:
         self.info = info.as_dict()
         self.status = rc
         return lam, H, lab, self.info
+
+    def backward_vectors(self, grad_H: torch.Tensor, grad_lambda: torch.Tensor | None = None,
+                         bandwidth: float | None = None, max_iter: int = 0, rtol: float = 0.0):
+        """d loss / d values (nnz,) for a loss on H (grad_H = d loss / d H, n x k) and optionally on the
+        eigenvalues; also d / d bandwidth, the CG iterations and the final relative residual."""
+        G = grad_H.to(device=self.device, dtype=torch.float64).contiguous()
+        gl = None if grad_lambda is None else grad_lambda.to(device=self.device, dtype=torch.float64).contiguous()
+        out = torch.empty(self.nnz, dtype=torch.float64, device=self.device)
+        gs, it, rr = B.sfairsc_backward_vectors(self.ctx, _ptr(G), _ptr(gl), _ptr(out), bandwidth or 0.0,
+                                                want_bandwidth=bandwidth is not None, max_iter=max_iter, rtol=rtol)
+        return out, gs, it, rr
 
     def backward(self, grad_lambda: torch.Tensor, bandwidth: float | None = None):
         """d(sum_i gbar_i lambda_i)/d values (nnz,) and optionally d/d bandwidth."""
@@ -130,6 +156,35 @@ class FairEigenvalueSum(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_lam):
         gv, gs = ctx.solver.backward(grad_lam, ctx.bw)
+        ctx.solver.close()
+        gbw = torch.tensor(gs, dtype=torch.float64, device=gv.device) if ctx.has_bw else None
+        return gv.to(ctx.values_dtype), None, None, None, None, None, gbw, None
+
+
+class FairEmbedding(torch.autograd.Function):
+    """(eigenvalues, H) of the fair problem as a differentiable function of the edge weights.
+
+    forward(values, row_ptr, col_idx, groups, k, h, bandwidth, opts) -> (eigenvalues (k,), H (n, k))
+    backward: d/d values (and d/d bandwidth) of any loss on both outputs, through the
+    eigenvector-level backward (conjugate-gradient solves and an SDDMM in the library).
+    """
+
+    @staticmethod
+    def forward(ctx, values, row_ptr, col_idx, groups, k, h, bandwidth=None, opts=None):
+        opts = dict(opts or {})
+        solver = FairSC(row_ptr, col_idx, values.detach(), groups, k, h, **opts)
+        lam, H, _, info = solver.solve(want_labels=False, allow_not_converged=True)
+        ctx.solver = solver
+        ctx.has_bw = isinstance(bandwidth, torch.Tensor)
+        ctx.bw = float(bandwidth) if ctx.has_bw else None
+        ctx.values_dtype = values.dtype
+        return lam, H
+
+    @staticmethod
+    def backward(ctx, grad_lam, grad_H):
+        if grad_H is None:
+            grad_H = torch.zeros(ctx.solver.n, ctx.solver.k, dtype=torch.float64, device=ctx.solver.device)
+        gv, gs, _, _ = ctx.solver.backward_vectors(grad_H, grad_lam, ctx.bw)
         ctx.solver.close()
         gbw = torch.tensor(gs, dtype=torch.float64, device=gv.device) if ctx.has_bw else None
         return gv.to(ctx.values_dtype), None, None, None, None, None, gbw, None

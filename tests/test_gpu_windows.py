@@ -61,13 +61,14 @@ def test_windowed_equals_plain_and_oracle(built_lib, prec, vdt):
     vals = g.values if vdt != torch.bfloat16 else g.values  # 0/1 weights are exact in every type
     op = SFairSCOperator(sp.csr_matrix((vals, g.col_idx, g.row_ptr), shape=(g.n, g.n)), g.groups, g.h)
     for nvec in (1, 2, 4):
-        w, out_w, info, sigma = run(g, prec, vdt, nvec, 0, seed=nvec)
-        _, out_p, info_p, _ = run(g, prec, vdt, nvec, -1, seed=nvec)
+        w, out_w, info, sigma = run(g, prec, vdt, nvec, 1, seed=nvec)
+        _, out_p, info_p, _ = run(g, prec, vdt, nvec, 0, seed=nvec)
+        # the two schedules sum each row's entries in the same order: the same bits
         assert np.array_equal(out_w, out_p), (prec, nvec)
         ref = op.apply(w)
         err = np.abs(out_w - ref).max() / (op.sigma * np.abs(w).max())
         assert err < (1e-13 if prec == "fp64" else 3e-6), (prec, nvec, err)
-        assert info["spmv_windowed"] > 0 and info["spmv_in_window"] > 0.5, info
+        assert info["spmv_windowed"] > 0 and info["spmv_in_window"] > 0.25, info
         assert info_p["spmv_windowed"] == 0
         assert info["max_resid"] <= 1e-6
 
@@ -75,7 +76,7 @@ def test_windowed_equals_plain_and_oracle(built_lib, prec, vdt):
 def test_shuffled_vertices_still_correct(built_lib):
     g = shuffled(clustered(120_000, 6, 3, 20, seed=32), seed=5)
     op = SFairSCOperator(sp.csr_matrix((g.values, g.col_idx, g.row_ptr), shape=(g.n, g.n)), g.groups, g.h)
-    w, out, info, _ = run(g, "mixed", torch.float32, 4, 0)
+    w, out, info, _ = run(g, "mixed", torch.float32, 4, 1)
     err = np.abs(out - op.apply(w)).max() / (op.sigma * np.abs(w).max())
     assert err < 3e-6, err
     assert info["spmv_in_window"] < 0.5, info
