@@ -44,6 +44,11 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-graph batched measurement")
     ap.add_argument("--scale", type=float, default=1.0, help="shrink n of the workload (profiling runs only)")
     ap.add_argument("--cpu-child", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--only", default=None, choices=["operator", "solve"],
+                    help="profiling runs: time the standalone operator (--nvec, --reps), or run one solve")
+    ap.add_argument("--nvec", type=int, default=1)
+    ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--window", type=int, default=0, help="spmv_window option of the context (0 or 1)")
     return ap.parse_args()
 
 
@@ -864,10 +869,55 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_only(args):
+    """--only operator: the standalone fused operator on the workload (nvec vectors, reps calls timed
+    with CUDA events after 3 untimed ones); --only solve: one create + solve with per-phase timing."""
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_2210_16435_gb300 import binding as B
+    from paper_2210_16435_gb300 import buildlib
+
+    buildlib.build()
+    from paper_2210_16435_gb300.solver import FairSC
+
+    c = load_workload(args.workload, args.scale)
+    g, k, h = c["graph"], c["k"], c["h"]
+    vdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[c["value_dtype"]]
+    T = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")
+    s = FairSC(T(g.row_ptr, torch.int32), T(g.col_idx, torch.int32), T(g.values, vdt), T(g.groups, torch.int32),
+               k=k, h=h, prec=args.prec, block=args.block, spmv_window=args.window, profile=1)
+    if args.only == "operator":
+        W = torch.randn(args.nvec, g.n, device="cuda", dtype=s.vec_dtype)
+        O = torch.empty_like(W)
+        for _ in range(3):
+            B.sfairsc_apply_operator(s.ctx, W.data_ptr(), O.data_ptr(), args.nvec)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.reps):
+            B.sfairsc_apply_operator(s.ctx, W.data_ptr(), O.data_ptr(), args.nvec)
+        e1.record()
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) / args.reps * 1e3
+        s_x = 8 if args.prec == "fp64" else 4
+        ob = operator_bytes(g.n, g.nnz, VDT_BYTES[c["value_dtype"]], s_x, args.nvec)
+        print(json.dumps({"only": "operator", "workload": args.workload, "nvec": args.nvec, "prec": args.prec,
+                          "window": args.window, "us": us, "gbs": ob / (us * 1e3)}), flush=True)
+    else:
+        _, _, _, inf = s.solve(want_labels=False)
+        print(json.dumps({"only": "solve", "workload": args.workload, **inf}), flush=True)
+    s.close()
+
+
 def main():
     args = parse()
     if args.cpu_child:
         oracle_single_thread_child(args)
+        return
+    if args.only:
+        run_only(args)
         return
     if args.workload == "msbm_batch256" and args.impl != "reference":
         run_batched_main(args)

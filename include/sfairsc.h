@@ -83,7 +83,7 @@ typedef struct {
   double sigma;            /* Hotelling shift; NaN => ||L_n||_1 (App. C) */
   double tol;              /* converged when ||A x - lambda x|| <= tol * sigma; default 1e-6 */
   int32_t max_restarts;    /* default 200 */
-  int32_t basis;           /* Krylov basis size m; 0 => max(2k, 20) rounded to the block */
+  int32_t basis;           /* Krylov basis size m; 0 => max(2k, 20, 10 b) rounded to the block b */
   int32_t prec;            /* sfairsc_prec; default MIXED */
   int32_t block;           /* Krylov block size 1..4; default 1 */
   uint64_t seed;           /* start block of the eigensolver; default 1 */

@@ -89,6 +89,7 @@ struct sfairsc_ctx {
   OpPlan proj64;  // FP64 projection P w only
   void* ytil = nullptr;
   double* ytil64 = nullptr;
+  double* dfT = nullptr;  // n x 4 FP64: L_n X of the final check (MIXED)
   double* op_partial = nullptr;
   int32_t* cta_rows = nullptr;
   int32_t* cta_rows_orth = nullptr;
@@ -367,6 +368,7 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   const size_t vs = c->vt == VecType::F64 ? 8 : 4;
   c->ytil = c->dalloc<unsigned char>((size_t)n * 4 * vs);
   c->ytil64 = c->dalloc<double>((size_t)n * 4);
+  c->dfT = c->vt == VecType::F32 ? c->dalloc<double>((size_t)n * 4) : nullptr;
   c->op_partial = c->dalloc<double>((size_t)grid * kMaxGroups * 4);
   // words: [0..1] the operator's 64-bit barrier counter, [2] error word,
   // [4..7] operator work counters, [8..9] the Gram-Schmidt kernel's counter
@@ -451,7 +453,9 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   // Krylov basis
   c->B = std::max(1, std::min(SFAIRSC_MAX_BLOCK, c->opts.block));
   if (c->B == 3) c->B = 4;
-  int m = c->opts.basis > 0 ? c->opts.basis : std::max(2 * c->k, 20);
+  // default basis: max(2k, 20) (the eigs default), and at least 10 b so that a block cycle still
+  // adds several blocks after a thick restart
+  int m = c->opts.basis > 0 ? c->opts.basis : std::max({2 * c->k, 20, 10 * c->B});
   m = std::max(m, c->k + c->B);
   m = (m + c->B - 1) / c->B * c->B;
   const int mcap = (n / c->B) * c->B - c->B;
@@ -637,9 +641,21 @@ double final_check(sfairsc_ctx* c, int mv, const std::vector<double>& T, std::ve
     const int nv = std::min(4, k - i);
     launch_operator(c->proj64, VecType::F64, c->AX64 + (size_t)i * n, 1, n, c->X64 + (size_t)i * n, 1, n, nv, s);
   }
-  for (int i = 0; i < k; i += 4) {
-    const int nv = std::min(4, k - i);
-    apply_op(c, true, c->X64 + (size_t)i * n, 1, n, c->AX64 + (size_t)i * n, 1, n, nv);
+  if (c->vt == VecType::F32) {
+    // X lies in null(C^T) (projected just above), so A X = P (L_n X): the SpMV in double-float on
+    // the FP32 pipe (FP64-grade), then the FP64 projection
+    for (int i = 0; i < k; i += 4) {
+      const int nv = std::min(4, k - i);
+      launch_df_spmv(n, c->row_ptr, c->col, c->val_orig, c->vdt_orig, c->dinv64, c->deg, c->normalized,
+                     c->op64.lanes_per_row, c->X64 + (size_t)i * n, nv, c->ytil64, c->dfT, c->sms, s);
+      launch_operator(c->proj64, VecType::F64, c->dfT, 1, n, c->AX64 + (size_t)i * n, 1, n, nv, s);
+      c->n_launches += 2 + (nv + 3) / 4;
+    }
+  } else {
+    for (int i = 0; i < k; i += 4) {
+      const int nv = std::min(4, k - i);
+      apply_op(c, true, c->X64 + (size_t)i * n, 1, n, c->AX64 + (size_t)i * n, 1, n, nv);
+    }
   }
   launch_column_stats(n, k, c->X64, c->AX64, nullptr, c->stat_partial, c->stat_blocks, nullptr, s);
   std::vector<double> st((size_t)c->stat_blocks * k * 3);

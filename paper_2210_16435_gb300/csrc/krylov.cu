@@ -160,12 +160,16 @@ __global__ void __launch_bounds__(256) tile_gemm_kernel(int n, VT* V, int64_t ld
   }
   if (MODE == 0) {
     __syncthreads();
+    VT* Es = Ys;  // the Y chunk's space is free now: E (m x B) in the basis precision
+    if (E)
+      for (int i = t; i < m * B; i += blockDim.x) Es[i] = (VT)E[i];
+    __syncthreads();
     for (int i = t; i < rows * B; i += blockDim.x) {
       const int rr = i / B, v = i % B;
       VT x = Vt[(size_t)(m + v) * kTS + rr];
       if (E) {  // the carried block's pending second projection: x -= V[r, 0:m] E[:, v]
         VT d = VT(0);
-        for (int c = 0; c < m; ++c) d = fma(Vt[(size_t)c * kTS + rr], (VT)E[c * B + v], d);
+        for (int c = 0; c < m; ++c) d = fma(Vt[(size_t)c * kTS + rr], Es[c * B + v], d);
         x -= d;
       }
       V[((K + v) >> 2) * pn + (size_t)(rbase + rr) * 4 + ((K + v) & 3)] = x;

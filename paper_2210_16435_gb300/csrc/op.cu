@@ -889,3 +889,179 @@ int operator_max_grid(VecType vt, int val_dtype, int nvec, int threads, size_t s
 }
 
 }  // namespace sfairsc
+
+namespace sfairsc {
+
+// ---------------------------------------------------------------- FP64-grade SpMV on the FP32 pipe
+// t = L_n x for FP64 vectors x (b columns), with FP64-grade accuracy but FP32 arithmetic: the
+// final residual check of the MIXED path applies the operator to Ritz vectors that already lie
+// in null(C^T) (the FP64 projection just before), so A x = P (L_n x) and only the SpMV needs the
+// precision.  GB300's FP64 rate would bound an FP64 SpMV; here every product and sum is carried
+// as an unevaluated pair of floats (hi + lo) with the error-free transforms TwoSum (Knuth) and
+// TwoProduct by FMA (Ogita, Rump and Oishi, 2005), about 2^-44 relative, far below the 1e-6
+// residual it verifies.  ytil = D^{-1/2} x is formed in FP64 and stored as (hi, lo) float pairs.
+namespace {
+
+struct F2 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ F2 split_f64(double v) {
+  const float hi = __double2float_rn(v);
+  return F2{hi, __double2float_rn(v - (double)hi)};
+}
+
+// s += w * y (w = w_hi + w_lo, y = y.hi + y.lo), the pair renormalised
+__device__ __forceinline__ void df_mac(F2& s, float w_hi, float w_lo, F2 y) {
+  const float p = __fmul_rn(w_hi, y.hi);
+  float pe = __fmaf_rn(w_hi, y.hi, -p);
+  pe = __fmaf_rn(w_hi, y.lo, pe);
+  pe = __fmaf_rn(w_lo, y.hi, pe);
+  float t, e;
+  two_sum(s.hi, p, t, e);
+  e = __fadd_rn(e, __fadd_rn(s.lo, pe));
+  s.hi = __fadd_rn(t, e);
+  s.lo = __fsub_rn(e, __fsub_rn(s.hi, t));
+}
+
+__device__ __forceinline__ F2 df_add(F2 a, F2 b) {
+  float t, e;
+  two_sum(a.hi, b.hi, t, e);
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  F2 r;
+  r.hi = __fadd_rn(t, e);
+  r.lo = __fsub_rn(e, __fsub_rn(r.hi, t));
+  return r;
+}
+
+template <typename MT>
+__device__ __forceinline__ void weight_split(MT v, float& hi, float& lo) {
+  if constexpr (sizeof(MT) == 8) {
+    hi = __double2float_rn((double)v);
+    lo = __double2float_rn((double)v - (double)hi);
+  } else {
+    hi = val_as<float>(v);  // BF16 and FP32 weights are exact floats
+    lo = 0.f;
+  }
+}
+
+__global__ void df_ytil_kernel(int n, int b, const double* __restrict__ X, const double* __restrict__ dinv,
+                               int normalized, F2* ytil) {
+  const int64_t total = (int64_t)n * b;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / b, v = e % b;
+    const double x = X[r + v * (int64_t)n];
+    ytil[e] = split_f64(normalized ? dinv[r] * x : x);
+  }
+}
+
+// Warp-per-row-group SpMV: Lr lanes per row, U pairs per lane per pass, row groups taken in turn
+// by the warps of the grid.  T[:, v] = x_v - d^{-1/2} (W ytil)_v  (normalized), d x_v - W x_v (not).
+template <typename MT, int B>
+__global__ void __launch_bounds__(256) df_spmv_kernel(int n, const int32_t* __restrict__ row_ptr,
+                                                      const int32_t* __restrict__ col, const MT* __restrict__ val,
+                                                      const double* __restrict__ dinv,
+                                                      const double* __restrict__ deg, int normalized, int Lr,
+                                                      const double* __restrict__ X, const F2* __restrict__ ytil,
+                                                      double* T) {
+  constexpr int U = 4;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane & (Lr - 1);
+  const int rpw = 32 / Lr;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  const int ngroups = (n + rpw - 1) / rpw;
+  for (int q = gw; q < ngroups; q += nw) {
+    const int r = q * rpw + lane / Lr;
+    const bool live = r < n;
+    const int e0 = live ? __ldg(row_ptr + r) : 0, e1 = live ? __ldg(row_ptr + r + 1) : 0;
+    F2 acc[B];
+#pragma unroll
+    for (int v = 0; v < B; ++v) acc[v] = F2{0.f, 0.f};
+    for (int e = e0 + sub; e < e1; e += U * Lr) {
+      int c[U];
+      float wh[U], wl[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int ee = e + u * Lr;
+        const bool in = ee < e1;
+        c[u] = in ? __ldg(col + ee) : -1;
+        if (in) weight_split<MT>(val[ee], wh[u], wl[u]);
+        else wh[u] = wl[u] = 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (c[u] >= 0) {
+          F2 y[B];
+          const F2* p = ytil + (size_t)c[u] * B;
+          if constexpr (B == 4) {
+            const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+            const float4 bb = __ldg(reinterpret_cast<const float4*>(p) + 1);
+            y[0] = F2{a.x, a.y};
+            y[1] = F2{a.z, a.w};
+            y[2] = F2{bb.x, bb.y};
+            y[3] = F2{bb.z, bb.w};
+          } else {
+#pragma unroll
+            for (int v = 0; v < B; ++v) y[v] = p[v];
+          }
+#pragma unroll
+          for (int v = 0; v < B; ++v) df_mac(acc[v], wh[u], wl[u], y[v]);
+        }
+      }
+    }
+    // pairs summed over the row's lanes by a fixed tree
+    for (int o = Lr >> 1; o > 0; o >>= 1)
+#pragma unroll
+      for (int v = 0; v < B; ++v) {
+        F2 other;
+        other.hi = __shfl_xor_sync(0xffffffffu, acc[v].hi, o);
+        other.lo = __shfl_xor_sync(0xffffffffu, acc[v].lo, o);
+        acc[v] = df_add(acc[v], other);
+      }
+    if (live && sub == 0) {
+#pragma unroll
+      for (int v = 0; v < B; ++v) {
+        const double s = (double)acc[v].hi + (double)acc[v].lo;
+        const double x = X[(size_t)r + (size_t)v * n];
+        T[(size_t)r + (size_t)v * n] = normalized ? x - dinv[r] * s : deg[r] * x - s;
+      }
+    }
+  }
+}
+
+template <typename MT>
+void df_spmv_launch(int n, const int32_t* row_ptr, const int32_t* col, const void* val, const double* dinv,
+                    const double* deg, int normalized, int Lr, const double* X, int b, F2* ytil, double* T, int sms,
+                    cudaStream_t s) {
+  df_ytil_kernel<<<4 * sms, 256, 0, s>>>(n, b, X, dinv, normalized, ytil);
+  const MT* v = static_cast<const MT*>(val);
+  const int grid = 8 * sms;
+  switch (b) {
+    case 4: df_spmv_kernel<MT, 4><<<grid, 256, 0, s>>>(n, row_ptr, col, v, dinv, deg, normalized, Lr, X, ytil, T); break;
+    case 3: df_spmv_kernel<MT, 3><<<grid, 256, 0, s>>>(n, row_ptr, col, v, dinv, deg, normalized, Lr, X, ytil, T); break;
+    case 2: df_spmv_kernel<MT, 2><<<grid, 256, 0, s>>>(n, row_ptr, col, v, dinv, deg, normalized, Lr, X, ytil, T); break;
+    default: df_spmv_kernel<MT, 1><<<grid, 256, 0, s>>>(n, row_ptr, col, v, dinv, deg, normalized, Lr, X, ytil, T);
+  }
+}
+
+}  // namespace
+
+void launch_df_spmv(int n, const int32_t* row_ptr, const int32_t* col, const void* val, int val_dtype,
+                    const double* dinv64, const double* deg, int normalized, int lanes, const double* X, int b,
+                    void* ytil_pairs, double* T, int sms, cudaStream_t s) {
+  if (b < 1 || b > 4) fail(SFAIRSC_ERR_INVALID_ARG, "df spmv block");
+  F2* yt = static_cast<F2*>(ytil_pairs);
+  switch (val_dtype) {
+    case SFAIRSC_F64:
+      df_spmv_launch<double>(n, row_ptr, col, val, dinv64, deg, normalized, lanes, X, b, yt, T, sms, s);
+      break;
+    case SFAIRSC_F32:
+      df_spmv_launch<float>(n, row_ptr, col, val, dinv64, deg, normalized, lanes, X, b, yt, T, sms, s);
+      break;
+    default:
+      df_spmv_launch<__nv_bfloat16>(n, row_ptr, col, val, dinv64, deg, normalized, lanes, X, b, yt, T, sms, s);
+  }
+  check_cuda(cudaGetLastError(), "df spmv launch");
+}
+
+}  // namespace sfairsc

@@ -120,6 +120,30 @@ __device__ __forceinline__ void st4(VT* p, const VT (&x)[4]) {
   }
 }
 
+// 4 * B consecutive coefficients (a panel's columns times the block's vectors) from shared
+// memory in 16-byte pieces (the array starts 16-byte aligned and 4 * B * sizeof(VT) is a
+// multiple of 16).
+template <typename VT, int B>
+__device__ __forceinline__ void ld_coefs(const VT* p, VT (&c)[4 * B]) {
+  if constexpr (sizeof(VT) == 4) {
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+      const float4 v = reinterpret_cast<const float4*>(p)[q];
+      c[4 * q] = v.x;
+      c[4 * q + 1] = v.y;
+      c[4 * q + 2] = v.z;
+      c[4 * q + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 2 * B; ++q) {
+      const double2 v = reinterpret_cast<const double2*>(p)[q];
+      c[2 * q] = v.x;
+      c[2 * q + 1] = v.y;
+    }
+  }
+}
+
 __device__ __forceinline__ int lanes_for(int np) {
   return np <= 1 ? 1 : np <= 2 ? 2 : np <= 4 ? 4 : np <= 8 ? 8 : np <= 16 ? 16 : 32;
 }
@@ -406,24 +430,27 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
           for (int v = 0; v < B; ++v) d1[v] = VT(0);
           int pp = g;
           for (; pp + LPA < nfull; pp += 2 * LPA) {
-            VT x0[4], x1[4];
+            VT x0[4], x1[4], c0[4 * B], c1[4 * B];
             ld4(at(i, pp), x0);
             ld4(at(i, pp + LPA), x1);
+            ld_coefs<VT, B>(cfs + 4 * pp * B, c0);  // a panel's 4 x B coefficients: 16-byte loads
+            ld_coefs<VT, B>(cfs + 4 * (pp + LPA) * B, c1);
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj)
 #pragma unroll
               for (int v = 0; v < B; ++v) {
-                d[v] = fma(x0[jj], cfs[(4 * pp + jj) * B + v], d[v]);
-                d1[v] = fma(x1[jj], cfs[(4 * (pp + LPA) + jj) * B + v], d1[v]);
+                d[v] = fma(x0[jj], c0[jj * B + v], d[v]);
+                d1[v] = fma(x1[jj], c1[jj * B + v], d1[v]);
               }
           }
           if (pp < nfull) {
-            VT x[4];
+            VT x[4], c0[4 * B];
             ld4(at(i, pp), x);
+            ld_coefs<VT, B>(cfs + 4 * pp * B, c0);
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj)
 #pragma unroll
-              for (int v = 0; v < B; ++v) d[v] = fma(x[jj], cfs[(4 * pp + jj) * B + v], d[v]);
+              for (int v = 0; v < B; ++v) d[v] = fma(x[jj], c0[jj * B + v], d[v]);
           }
           if (nfull < np && (nfull & (LPA - 1)) == g) {
             VT x[4];
