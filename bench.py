@@ -537,13 +537,22 @@ def backward_bench(dev, peak):
     a1.record(stream)
     torch.cuda.synchronize()
     ms = a0.elapsed_time(a1) / reps
+    # the eigenvector-level backward (a loss on H): k conjugate-gradient solves on the FP64 operator + SDDMM
+    Gh = torch.randn(g.n, k, dtype=torch.float64, device=dev, generator=torch.Generator(device=dev).manual_seed(0))
+    s.backward_vectors(Gh, gl, bw)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, _, cg_it, cg_rr = s.backward_vectors(Gh, gl, bw)
+    torch.cuda.synchronize()
+    vec_s = time.perf_counter() - t0
     s.close()
     # stored entries: column index + FP32 weight read, FP64 gradient written; H rows read once per row
     bytes_ = g.nnz * (4 + 4) + g.n * k * 8 + g.nnz * 8 + 4 * (g.n + 1)
     gbs = bytes_ / (ms * 1e6)
     return {"workload": "msbm_n200k_k10_h4_gauss", "n": g.n, "nnz": g.nnz, "k": k, "forward_solve_s": t_fwd,
             "forward_restarts": inf["restarts"], "backward_ms": ms, "backward_bytes": bytes_,
-            "achieved_gbs": gbs, "frac": gbs / peak,
+            "achieved_gbs": gbs, "frac": gbs / peak, "vector_backward_s": vec_s, "vector_backward_cg_iterations": cg_it,
+            "vector_backward_cg_rel_resid": cg_rr,
             "fd_check": "tests/test_gpu_backward.py::test_differentiation_workload_full_size"}
 
 

@@ -1212,7 +1212,7 @@ int sfairsc_backward(sfairsc_ctx* ctx, const double* grad_lambda, double* grad_v
     if (grad_bandwidth) {
       double acc = 0.0;
       for (double v : part) acc += v;
-      *grad_bandwidth = bw > 0.0 ? acc : 0.0;
+      *grad_bandwidth = bw > 0.0 ? acc / bw : 0.0;  // the kernel sums g_e w_e (-2 ln w_e); dw/ds has the 1/s
     }
     check_cuda(cudaStreamSynchronize(s), "backward end");
   });
@@ -1370,7 +1370,7 @@ int sfairsc_backward_vectors(sfairsc_ctx* ctx, const double* grad_H, const doubl
     if (grad_bandwidth) {
       double acc = 0.0;
       for (double v : bp) acc += v;
-      *grad_bandwidth = bw > 0.0 ? acc : 0.0;
+      *grad_bandwidth = bw > 0.0 ? acc / bw : 0.0;
     }
     if (iterations) *iterations = it;
     if (max_rel_resid) *max_rel_resid = worst;

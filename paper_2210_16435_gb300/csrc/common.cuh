@@ -126,6 +126,53 @@ struct Comp32 {
   }
 };
 
+// Warp reduce-scatter of N compensated accumulators (N a power of two, 1..32):
+// recursive halving over lane bits 16, 8, ... -- at each level a lane keeps the
+// half of its accumulators selected by that bit of its lane id and receives its
+// partner's copy of the same half, adding by TwoSum -- then plain halving of the
+// one remaining accumulator over the lower lane bits.  Afterwards lane L holds
+// in acc[0] the full warp sum of accumulator scatter_index<N>(L) (lanes that
+// differ only in bits below log2(N) hold the same sum).  N + ... + 1 exchanges
+// instead of 5 N for a butterfly on every accumulator; the order of the adds
+// is fixed, so the result is bitwise reproducible.
+template <int N>
+__device__ __forceinline__ int scatter_index(int lane) {
+  int idx = 0;
+#pragma unroll
+  for (int half = N / 2, o = 16; half >= 1; half >>= 1, o >>= 1)
+    if (lane & o) idx += half;
+  return idx;
+}
+
+__device__ __forceinline__ Comp32 comp32_combine(Comp32 a, float os, float oc) {
+  float t, e;
+  two_sum(a.s, os, t, e);
+  Comp32 r;
+  r.s = t;
+  r.c = __fadd_rn(__fadd_rn(a.c, oc), e);
+  return r;
+}
+
+template <int N>
+__device__ __forceinline__ void comp32_reduce_scatter(Comp32 (&acc)[N], int lane) {
+  int o = 16;
+#pragma unroll
+  for (int half = N / 2; half >= 1; half >>= 1, o >>= 1) {
+    const bool upper = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const Comp32 lo = acc[i], hi = acc[i + half];
+      const Comp32 send = upper ? lo : hi, keep = upper ? hi : lo;
+      const float rs = __shfl_xor_sync(0xffffffffu, send.s, o), rc = __shfl_xor_sync(0xffffffffu, send.c, o);
+      acc[i] = comp32_combine(keep, rs, rc);
+    }
+  }
+  for (; o >= 1; o >>= 1) {
+    const float rs = __shfl_xor_sync(0xffffffffu, acc[0].s, o), rc = __shfl_xor_sync(0xffffffffu, acc[0].c, o);
+    acc[0] = comp32_combine(acc[0], rs, rc);
+  }
+}
+
 // Sum of n packed pairs p[0], p[stride], ... (Comp32::slot) by TwoSum in
 // FP32, in order, converted to FP64 once.
 __device__ __forceinline__ double comp32_slot_sum(const double* p, int n, int stride) {

@@ -66,11 +66,13 @@ __device__ __forceinline__ int scale_shift(float maxv, long long n) {
   return 62 - (64 - __clzll((unsigned long long)n)) - e;
 }
 
-__device__ __forceinline__ float dist_rn(const float* x, const float* m, int d) {
+// sum over j in order of (x_j - m_j)^2, each operation rounded once; the subtract and the add run
+// as fma(., +-one, .) with one = 1 from the launch (exact like a plain add, on the FMA pipe)
+__device__ __forceinline__ float dist_rn(const float* x, const float* m, int d, float one) {
   float acc = 0.f;
   for (int j = 0; j < d; ++j) {
-    const float t = __fsub_rn(x[j], m[j]);
-    acc = __fadd_rn(acc, __fmul_rn(t, t));
+    const float t = __fmaf_rn(m[j], -one, x[j]);
+    acc = __fmaf_rn(acc, one, __fmul_rn(t, t));
   }
   return acc;
 }
@@ -90,7 +92,7 @@ __global__ void to_f32_kernel(long long nd, const double* __restrict__ X, float*
 // ---------------------------------------------------------------- k-means++ seeding
 // D2 <- (t == 1 ? dist(x, c) : min(D2, dist(x, c))) for the newest center c; block maxima.
 __global__ void seed_dist_kernel(int n, int d, const float* __restrict__ X32, int k, const int* __restrict__ centers,
-                                 int t, float* D2, unsigned* blockmax) {
+                                 int t, float* D2, unsigned* blockmax, float one) {
   extern __shared__ float csh[];
   const int r = blockIdx.y;
   const int c = centers[r * k + t - 1];
@@ -99,7 +101,7 @@ __global__ void seed_dist_kernel(int n, int d, const float* __restrict__ X32, in
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   unsigned mb = 0;
   if (i < n) {
-    float v = dist_rn(X32 + (size_t)i * d, csh, d);
+    float v = dist_rn(X32 + (size_t)i * d, csh, d, one);
     float* p = D2 + (size_t)r * n + i;
     if (t > 1) v = fminf(*p, v);
     *p = v;
@@ -259,9 +261,12 @@ __device__ __forceinline__ unsigned long long mul2_rn(unsigned long long a, unsi
 // one packed pair, and two centroids are scanned together (two independent
 // sums).  An odd dimension count is padded with x = m = 0, whose +0 term
 // leaves the sum unchanged.
+// The adds of the distance sums run as fma(a, one, b) with one = 1 passed at launch (opaque to the
+// compiler): a * 1 is exact, so each rounds a + b once exactly as an add does, but issues on the
+// FMA pipe (plain FP32 adds share a narrower pipe on this GPU).
 template <int DMAX>
 __global__ void assign_kernel(int n, int d, int k, const float* __restrict__ X32, const double* __restrict__ mu,
-                              int* lab, float* dist, unsigned* changed, const int* __restrict__ done) {
+                              int* lab, float* dist, unsigned* changed, const int* __restrict__ done, float one) {
   static_assert(DMAX % 2 == 0, "dimension pairs");
   extern __shared__ float msh[];  // k x dp, dp = d rounded up to even, zero padded
   const int r = blockIdx.y;
@@ -305,8 +310,8 @@ __global__ void assign_kernel(int n, int d, int k, const float* __restrict__ X32
           float s00, s01, s10, s11;
           unpack2(mul2_rn(t0, t0), s00, s01);
           unpack2(mul2_rn(t1, t1), s10, s11);
-          a0 = __fadd_rn(__fadd_rn(a0, s00), s01);
-          a1 = __fadd_rn(__fadd_rn(a1, s10), s11);
+          a0 = __fmaf_rn(__fmaf_rn(a0, one, s00), one, s01);
+          a1 = __fmaf_rn(__fmaf_rn(a1, one, s10), one, s11);
         }
       }
       if (c == 0 || a0 < best) {
@@ -443,7 +448,7 @@ __global__ void finalize_kernel(int n, int d, int k, const float* __restrict__ X
 
 // Inertia: distance of each row to its own centroid; max, then exact quantised sum.
 __global__ void own_dist_kernel(int n, int d, int k, const float* __restrict__ X32, const double* __restrict__ mu,
-                                const int* __restrict__ lab, float* dist, unsigned* maxbits) {
+                                const int* __restrict__ lab, float* dist, unsigned* maxbits, float one) {
   extern __shared__ float msh[];
   const int r = blockIdx.y;
   for (int i = threadIdx.x; i < k * d; i += blockDim.x) msh[i] = __double2float_rn(mu[(size_t)r * k * d + i]);
@@ -452,7 +457,7 @@ __global__ void own_dist_kernel(int n, int d, int k, const float* __restrict__ X
   unsigned mb = 0;
   if (i < n) {
     const int c = lab[(size_t)r * n + i];
-    const float v = dist_rn(X32 + (size_t)i * d, msh + c * d, d);
+    const float v = dist_rn(X32 + (size_t)i * d, msh + c * d, d, one);
     dist[(size_t)r * n + i] = v;
     mb = __float_as_uint(v);
   }
@@ -538,7 +543,7 @@ KmeansResult run_kmeans(int64_t n64, int d, const double* X, int kc, uint64_t se
     check_cuda(cudaStreamSynchronize(s), "k-means upload");  // host vectors go out of scope below
     res.launches = 1 + 4 * (k - 1) + 1;
     for (int t = 1; t < k; ++t) {
-      seed_dist_kernel<<<dim3(nb, R), bs, sizeof(float) * d, s>>>(n, d, X32, k, centers, t, D2, blockmax);
+      seed_dist_kernel<<<dim3(nb, R), bs, sizeof(float) * d, s>>>(n, d, X32, k, centers, t, D2, blockmax, 1.f);
       seed_gmax_kernel<<<R, 1024, 0, s>>>(nb, blockmax, gmax);
       seed_qsum_kernel<<<dim3(nb, R), bs, 0, s>>>(n, D2, gmax, blocksum);
       seed_select_kernel<<<R, 1024, 0, s>>>(n, nb, bs, D2, gmax, blocksum, r64, k, t, centers);
@@ -566,13 +571,13 @@ KmeansResult run_kmeans(int64_t n64, int d, const double* X, int kc, uint64_t se
     auto assign = [&](void) {
       if (d <= 16) {
         check_cuda(cudaFuncSetAttribute(assign_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)amsmem), "attr");
-        assign_kernel<16><<<dim3(nb, R), bs, amsmem, s>>>(n, d, k, X32, mu, lab, dist, changed, done);
+        assign_kernel<16><<<dim3(nb, R), bs, amsmem, s>>>(n, d, k, X32, mu, lab, dist, changed, done, 1.f);
       } else if (d <= 32) {
         check_cuda(cudaFuncSetAttribute(assign_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)amsmem), "attr");
-        assign_kernel<32><<<dim3(nb, R), bs, amsmem, s>>>(n, d, k, X32, mu, lab, dist, changed, done);
+        assign_kernel<32><<<dim3(nb, R), bs, amsmem, s>>>(n, d, k, X32, mu, lab, dist, changed, done, 1.f);
       } else {
         check_cuda(cudaFuncSetAttribute(assign_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)amsmem), "attr");
-        assign_kernel<64><<<dim3(nb, R), bs, amsmem, s>>>(n, d, k, X32, mu, lab, dist, changed, done);
+        assign_kernel<64><<<dim3(nb, R), bs, amsmem, s>>>(n, d, k, X32, mu, lab, dist, changed, done, 1.f);
       }
     };
     std::vector<int> hdone(R);
@@ -589,7 +594,7 @@ KmeansResult run_kmeans(int64_t n64, int d, const double* X, int kc, uint64_t se
       }
     }
     res.launches += 3;
-    own_dist_kernel<<<dim3(nb, R), bs, msmem, s>>>(n, d, k, X32, mu, lab, dist, maxd);
+    own_dist_kernel<<<dim3(nb, R), bs, msmem, s>>>(n, d, k, X32, mu, lab, dist, maxd, 1.f);
     qsum_all_kernel<<<dim3(nb, R), bs, 0, s>>>(n, dist, maxd, tot);
     check_cuda(cudaGetLastError(), "inertia launch");
     std::vector<unsigned> hmax(R);

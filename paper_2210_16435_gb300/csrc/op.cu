@@ -186,15 +186,14 @@ __device__ void cta_group_sums(int r0, int r1, int h, const uint8_t* __restrict_
   const int P = h * B;
   for (int s0 = 0; s0 < h; s0 += 4) {
     if constexpr (sizeof(VT) == 4) {
-      float win[4][B];
-      Comp32 acc[4][B];
+      constexpr int NA = 4 * B;  // accumulator j * B + v: group s0 + j, vector v
+      float win[NA];
+      Comp32 acc[NA];
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int v = 0; v < B; ++v) {
-          win[j][v] = 0.f;
-          acc[j][v].zero();
-        }
+      for (int q = 0; q < NA; ++q) {
+        win[q] = 0.f;
+        acc[q].zero();
+      }
       int cnt = 0;
       const int T = blockDim.x;
       constexpr int RF = B == 4 ? 2 : 4;  // rows in flight (fewer at B = 4: registers)
@@ -216,29 +215,25 @@ __device__ void cta_group_sums(int r0, int r1, int h, const uint8_t* __restrict_
 #pragma unroll
           for (int j = 0; j < 4; ++j)
 #pragma unroll
-            for (int v = 0; v < B; ++v) win[j][v] += g[k] == j ? x[k][v] : 0.f;
+            for (int v = 0; v < B; ++v) win[j * B + v] += g[k] == j ? x[k][v] : 0.f;
         if (++cnt == 16 / RF) {  // windows of 16 rows
 #pragma unroll
-          for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int v = 0; v < B; ++v) {
-              acc[j][v].add(win[j][v]);
-              win[j][v] = 0.f;
-            }
+          for (int q = 0; q < NA; ++q) {
+            acc[q].add(win[q]);
+            win[q] = 0.f;
+          }
           cnt = 0;
         }
       }
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int v = 0; v < B; ++v) {
-          acc[j][v].add(win[j][v]);
-          acc[j][v].reduce(1);
-        }
-      if (lane == 0)
-        for (int j = 0; j < 4 && s0 + j < h; ++j)
-#pragma unroll
-          for (int v = 0; v < B; ++v) red[warp * P + (s0 + j) * B + v] = acc[j][v].slot();
+      for (int q = 0; q < NA; ++q) acc[q].add(win[q]);
+      // the accumulators over the warp by one reduce-scatter tree; lane L then holds
+      // accumulator scatter_index(L)
+      comp32_reduce_scatter<NA>(acc, lane);
+      {
+        const int q = scatter_index<NA>(lane), j = q / B, v = q % B;
+        if ((lane & (32 / NA - 1)) == 0 && s0 + j < h) red[warp * P + (s0 + j) * B + v] = acc[0].slot();
+      }
     } else {
       double acc[4][B];
 #pragma unroll
@@ -322,17 +317,19 @@ __device__ void cta_dense_sums(int r0, int r1, int p, const VT* __restrict__ Fd,
           cnt = 0;
         }
       }
+      Comp32 fl[4 * B];
 #pragma unroll
       for (int j = 0; j < 4; ++j)
 #pragma unroll
         for (int v = 0; v < B; ++v) {
           acc[j][v].add(win[j][v]);
-          acc[j][v].reduce(1);
+          fl[j * B + v] = acc[j][v];
         }
-      if (lane == 0)
-        for (int j = 0; j < 4 && s0 + j < p; ++j)
-#pragma unroll
-          for (int v = 0; v < B; ++v) red[warp * P + (s0 + j) * B + v] = acc[j][v].slot();
+      comp32_reduce_scatter<4 * B>(fl, lane);
+      {
+        const int q = scatter_index<4 * B>(lane), j = q / B, v = q % B;
+        if ((lane & (32 / (4 * B) - 1)) == 0 && s0 + j < p) red[warp * P + (s0 + j) * B + v] = fl[0].slot();
+      }
     } else {
       double acc[4][B];
 #pragma unroll
@@ -911,26 +908,41 @@ __device__ __forceinline__ F2 split_f64(double v) {
   return F2{hi, __double2float_rn(v - (double)hi)};
 }
 
+// Sums and differences as fused multiply-adds with a multiplier of +-1 that the compiler cannot
+// see (a kernel argument): a * 1 is exact, so fma(a, 1, b) rounds a + b once, bit for bit like an
+// add, but issues on the FMA pipe (plain FP32 adds share a narrower pipe on this GPU).
+struct FmaAdd {
+  float one;
+  __device__ __forceinline__ float add(float a, float b) const { return __fmaf_rn(a, one, b); }
+  __device__ __forceinline__ float sub(float a, float b) const { return __fmaf_rn(b, -one, a); }
+  // TwoSum (Knuth): s + e == a + b exactly
+  __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) const {
+    s = add(a, b);
+    const float bb = sub(s, a);
+    e = add(sub(a, sub(s, bb)), sub(b, bb));
+  }
+};
+
 // s += w * y (w = w_hi + w_lo, y = y.hi + y.lo), the pair renormalised
-__device__ __forceinline__ void df_mac(F2& s, float w_hi, float w_lo, F2 y) {
+__device__ __forceinline__ void df_mac(const FmaAdd& f, F2& s, float w_hi, float w_lo, F2 y) {
   const float p = __fmul_rn(w_hi, y.hi);
   float pe = __fmaf_rn(w_hi, y.hi, -p);
   pe = __fmaf_rn(w_hi, y.lo, pe);
   pe = __fmaf_rn(w_lo, y.hi, pe);
   float t, e;
-  two_sum(s.hi, p, t, e);
-  e = __fadd_rn(e, __fadd_rn(s.lo, pe));
-  s.hi = __fadd_rn(t, e);
-  s.lo = __fsub_rn(e, __fsub_rn(s.hi, t));
+  f.two_sum(s.hi, p, t, e);
+  e = f.add(e, f.add(s.lo, pe));
+  s.hi = f.add(t, e);
+  s.lo = f.sub(e, f.sub(s.hi, t));
 }
 
-__device__ __forceinline__ F2 df_add(F2 a, F2 b) {
+__device__ __forceinline__ F2 df_add(const FmaAdd& f, F2 a, F2 b) {
   float t, e;
-  two_sum(a.hi, b.hi, t, e);
-  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  f.two_sum(a.hi, b.hi, t, e);
+  e = f.add(e, f.add(a.lo, b.lo));
   F2 r;
-  r.hi = __fadd_rn(t, e);
-  r.lo = __fsub_rn(e, __fsub_rn(r.hi, t));
+  r.hi = f.add(t, e);
+  r.lo = f.sub(e, f.sub(r.hi, t));
   return r;
 }
 
@@ -963,8 +975,9 @@ __global__ void __launch_bounds__(256) df_spmv_kernel(int n, const int32_t* __re
                                                       const double* __restrict__ dinv,
                                                       const double* __restrict__ deg, int normalized, int Lr,
                                                       const double* __restrict__ X, const F2* __restrict__ ytil,
-                                                      double* T) {
+                                                      double* T, float one) {
   constexpr int U = 4;
+  const FmaAdd fa{one};
   const int lane = threadIdx.x & 31;
   const int sub = lane & (Lr - 1);
   const int rpw = 32 / Lr;
@@ -1005,7 +1018,7 @@ __global__ void __launch_bounds__(256) df_spmv_kernel(int n, const int32_t* __re
             for (int v = 0; v < B; ++v) y[v] = p[v];
           }
 #pragma unroll
-          for (int v = 0; v < B; ++v) df_mac(acc[v], wh[u], wl[u], y[v]);
+          for (int v = 0; v < B; ++v) df_mac(fa, acc[v], wh[u], wl[u], y[v]);
         }
       }
     }
@@ -1016,7 +1029,7 @@ __global__ void __launch_bounds__(256) df_spmv_kernel(int n, const int32_t* __re
         F2 other;
         other.hi = __shfl_xor_sync(0xffffffffu, acc[v].hi, o);
         other.lo = __shfl_xor_sync(0xffffffffu, acc[v].lo, o);
-        acc[v] = df_add(acc[v], other);
+        acc[v] = df_add(fa, acc[v], other);
       }
     if (live && sub == 0) {
 #pragma unroll
@@ -1037,10 +1050,10 @@ void df_spmv_launch(int n, const int32_t* row_ptr, const int32_t* col, const voi
   const MT* v = static_cast<const MT*>(val);
   const int grid = 8 * sms;
   switch (b) {
-    case 4: df_spmv_kernel<MT, 4><<<grid, 256, 0, s>>>(n, row_ptr, col, v, dinv, deg, normalized, Lr, X, ytil, T); break;
-    case 3: df_spmv_kernel<MT, 3><<<grid, 256, 0, s>>>(n, row_ptr, col, v, dinv, deg, normalized, Lr, X, ytil, T); break;
-    case 2: df_spmv_kernel<MT, 2><<<grid, 256, 0, s>>>(n, row_ptr, col, v, dinv, deg, normalized, Lr, X, ytil, T); break;
-    default: df_spmv_kernel<MT, 1><<<grid, 256, 0, s>>>(n, row_ptr, col, v, dinv, deg, normalized, Lr, X, ytil, T);
+    case 4: df_spmv_kernel<MT, 4><<<grid, 256, 0, s>>>(n, row_ptr, col, v, dinv, deg, normalized, Lr, X, ytil, T, 1.f); break;
+    case 3: df_spmv_kernel<MT, 3><<<grid, 256, 0, s>>>(n, row_ptr, col, v, dinv, deg, normalized, Lr, X, ytil, T, 1.f); break;
+    case 2: df_spmv_kernel<MT, 2><<<grid, 256, 0, s>>>(n, row_ptr, col, v, dinv, deg, normalized, Lr, X, ytil, T, 1.f); break;
+    default: df_spmv_kernel<MT, 1><<<grid, 256, 0, s>>>(n, row_ptr, col, v, dinv, deg, normalized, Lr, X, ytil, T, 1.f);
   }
 }
 
