@@ -109,7 +109,11 @@ typedef struct {
                               projection and corrected during the next step's first pass over the basis
                               (two passes over the basis per step); 1: the DGKS test of ARPACK, a third
                               pass when a column kept less than 1/sqrt(2) of its norm */
-  int32_t reserved[4];
+  int32_t restart_mode;    /* the thick-restart product V <- V Y.  0 (default): on the tensor cores
+                              (tcgen05, TF32 in three passes hi*hi + hi*lo + lo*hi, FP32 accumulation) for
+                              a MIXED basis with blocks of 4 whose tile plan fits in shared memory, on the
+                              CUDA cores (FP32 FMA) otherwise; 1: always on the CUDA cores */
+  int32_t reserved[3];
 } sfairsc_opts;
 
 typedef struct {
@@ -140,7 +144,8 @@ typedef struct {
   int32_t spmv_segments;   /* row segments of the operator's SpMV at the solve's block size */
   int32_t spmv_windowed;   /* of those, segments that stage a shared-memory window of the input */
   float spmv_in_window;    /* fraction of the stored entries whose gather is served by a window */
-  int32_t reserved[4];
+  int32_t restarts_tc;     /* thick restarts taken on the tensor cores (opts.restart_mode) */
+  int32_t reserved[3];
 } sfairsc_info;
 
 typedef struct sfairsc_ctx sfairsc_ctx;
@@ -287,8 +292,12 @@ SFAIRSC_API int sfairsc_backward(sfairsc_ctx* ctx, const double* grad_lambda, do
  * bandwidth, grad_bandwidth   as in sfairsc_backward
  * max_iter      conjugate-gradient iterations (0: 1000); rtol relative residual (<= 0: 1e-10)
  * iterations, max_rel_resid   (nullable) iterations taken and the largest final relative residual
- * Errors: INVALID_ARG (no solve, repeated eigenvalue), UNSUPPORTED (k > 64, normalized = 0), CUDA, OOM,
- * DEVICE_TIMEOUT.
+ * The solves deflate with the computed eigenvectors, so they must come from an FP64 solve at a
+ * tolerance near rtol (for example opts.tol = 1e-12); a looser solve leaves parts of lower
+ * eigenvectors in the complement, where A - lambda_i I is indefinite, and the solves stall.
+ * Errors: INVALID_ARG (no solve, repeated eigenvalue), UNSUPPORTED (k > 64, normalized = 0, a MIXED
+ * context), NOT_CONVERGED (some relative residual above rtol after max_iter; outputs written from the
+ * last iterate), CUDA, OOM, DEVICE_TIMEOUT.
  */
 SFAIRSC_API int sfairsc_backward_vectors(sfairsc_ctx* ctx, const double* grad_H, const double* grad_lambda,
                                          double* grad_values, double bandwidth, double* grad_bandwidth,

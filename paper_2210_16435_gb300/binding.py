@@ -29,7 +29,7 @@ class Opts(ctypes.Structure):
         ("seed", ctypes.c_uint64), ("kmeans_seed", ctypes.c_uint64), ("kmeans_n_init", ctypes.c_int32),
         ("kmeans_max_iter", ctypes.c_int32), ("validate", ctypes.c_int32), ("profile", ctypes.c_int32),
         ("wait_limit_us", ctypes.c_int32), ("fault_inject", ctypes.c_int32), ("spmv_window", ctypes.c_int32),
-        ("orth_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4),
+        ("orth_mode", ctypes.c_int32), ("restart_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3),
     ]
 
 
@@ -44,7 +44,8 @@ class Info(ctypes.Structure):
         ("orth_cols", ctypes.c_int32), ("basis", ctypes.c_int32), ("block", ctypes.c_int32),
         ("orth_sweeps", ctypes.c_int32), ("ms_restart", ctypes.c_float), ("ms_host_eig", ctypes.c_float),
         ("ms_final", ctypes.c_float), ("host_eig_fallbacks", ctypes.c_int32), ("spmv_segments", ctypes.c_int32),
-        ("spmv_windowed", ctypes.c_int32), ("spmv_in_window", ctypes.c_float), ("reserved", ctypes.c_int32 * 4),
+        ("spmv_windowed", ctypes.c_int32), ("spmv_in_window", ctypes.c_float), ("restarts_tc", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
     ]
 
     def as_dict(self):
@@ -283,7 +284,7 @@ def sfairsc_solve_batched(graphs, opts=None, stream=None, allow=(0,)):
 
 def make_opts(prec="mixed", block=1, tol=1e-6, basis=0, max_restarts=200, sigma=None, seed=1, kmeans_seed=0,
               kmeans_n_init=1, kmeans_max_iter=100, validate=1, profile=0, wait_limit_us=0, fault_inject=0,
-              spmv_window=0, orth_mode=0) -> Opts:
+              spmv_window=0, orth_mode=0, restart_mode=0) -> Opts:
     o = sfairsc_opts_default()
     o.prec = SFAIRSC_PREC_FP64 if prec == "fp64" else SFAIRSC_PREC_MIXED
     o.block = int(block)
@@ -301,4 +302,5 @@ def make_opts(prec="mixed", block=1, tol=1e-6, basis=0, max_restarts=200, sigma=
     o.fault_inject = int(fault_inject)
     o.spmv_window = int(spmv_window)
     o.orth_mode = int(orth_mode)
+    o.restart_mode = int(restart_mode)
     return o

@@ -18,7 +18,7 @@ OBJDIR = os.path.join(LIBDIR, "obj")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIBNAME = "libsfairsc.so"
 
-SOURCES = ["setup.cu", "op.cu", "orth.cu", "krylov.cu", "kmeans.cu", "backward.cu", "api.cu", "static_op.cu", "window.cu", "vector_grad.cu", "batched.cu", "eig_host.cpp"]
+SOURCES = ["setup.cu", "op.cu", "orth.cu", "krylov.cu", "kmeans.cu", "backward.cu", "api.cu", "static_op.cu", "window.cu", "vector_grad.cu", "restart_tc.cu", "batched.cu", "eig_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
            "--expt-relaxed-constexpr", "-I" + INCLUDE]

@@ -104,6 +104,7 @@ struct sfairsc_ctx {
   void* Q = nullptr;
   double* Hd = nullptr;
   double* Yd = nullptr;
+  float* Ytc = nullptr;  // [Y | -E]^T split for the tensor-core restart (FP32 basis)
   double* orth_partial = nullptr;
   double* orth_coef = nullptr;
   OrthPlan orth;
@@ -474,6 +475,7 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   check_cuda(cudaMemsetAsync(c->Q, 0, (size_t)n * 4 * vs, s), "memset");
   c->Hd = c->dalloc<double>((size_t)c->ldh * m);
   c->Yd = c->dalloc<double>((size_t)m * m);
+  if (c->vt == VecType::F32) c->Ytc = c->dalloc<float>(2 * (size_t)((c->ldv + 7) / 8 * 8) * 256);
   const int ogmax = orth_max_grid(c->vt, c->B, 512);
   const int ogrid = std::max(1, std::min(ogmax, (n + 511) / 512));
   const int stride = 2 * 128 * 4 + 4 + 32;
@@ -804,8 +806,14 @@ int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* label
         eb = c->take_event();
         check_cuda(cudaEventRecord(ea, s), "event record");
       }
-      launch_restart(c->vt, n, c->V, c->ldv, mv, K, B, c->Yd, c->Q,
-                     (c->opts.orth_mode == 0 && !broke) ? c->orth.pend : nullptr, s);
+      const double* E = (c->opts.orth_mode == 0 && !broke) ? c->orth.pend : nullptr;
+      if (c->vt == VecType::F32 && c->opts.restart_mode == 0 && restart_tc_fits(n, c->ldv, mv, K, B)) {
+        launch_restart_tc(n, static_cast<float*>(c->V), c->ldv, mv, K, B, reinterpret_cast<const float*>(c->Yd),
+                          static_cast<float*>(c->Q), E, c->Ytc, c->sms, c->err, c->orth.wait_ns, s);
+        ++inf.restarts_tc;
+        c->n_launches += 1;  // the split of [Y | -E]
+      } else
+        launch_restart(c->vt, n, c->V, c->ldv, mv, K, B, c->Yd, c->Q, E, s);
       if (c->opts.profile) {
         check_cuda(cudaEventRecord(eb, s), "event record");
         c->ev_restart.emplace_back(ea, eb);
@@ -1012,7 +1020,7 @@ static bool valid_opts(const sfairsc_opts& o) {
   return o.tol > 0.0 && o.max_restarts >= 0 && o.block >= 1 && o.block <= SFAIRSC_MAX_BLOCK && o.kmeans_n_init >= 1 &&
          o.kmeans_max_iter >= 1 && (o.prec == 0 || o.prec == 1) && o.wait_limit_us >= 0 &&
          (o.fault_inject == 0 || o.fault_inject == 1) && (o.spmv_window == 0 || o.spmv_window == 1) &&
-         (o.orth_mode == 0 || o.orth_mode == 1);
+         (o.orth_mode == 0 || o.orth_mode == 1) && (o.restart_mode == 0 || o.restart_mode == 1);
 }
 
 int sfairsc_create(sfairsc_ctx** out, int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
@@ -1230,7 +1238,14 @@ int sfairsc_backward_vectors(sfairsc_ctx* ctx, const double* grad_H, const doubl
     g_last_error = "the eigenvector-level backward supports the normalized problem with k <= 64";
     return SFAIRSC_ERR_UNSUPPORTED;
   }
-  return guarded([&] {
+  if (ctx->opts.prec != SFAIRSC_PREC_FP64) {
+    // the solves below deflate with the computed eigenvectors: FP32-accurate ones leave components of
+    // lower eigenvectors in the complement, where A - lambda_i I is then indefinite
+    g_last_error = "the eigenvector-level backward needs the eigenvectors of an FP64 solve";
+    return SFAIRSC_ERR_UNSUPPORTED;
+  }
+  int status = SFAIRSC_OK;
+  const int rc = guarded([&] {
     cudaStream_t s = ctx->stream;
     const int n = (int)ctx->n, k = ctx->k;
     const int iters_max = max_iter > 0 ? max_iter : 1000;
@@ -1374,7 +1389,12 @@ int sfairsc_backward_vectors(sfairsc_ctx* ctx, const double* grad_H, const doubl
     }
     if (iterations) *iterations = it;
     if (max_rel_resid) *max_rel_resid = worst;
+    if (!(worst <= tol)) status = SFAIRSC_ERR_NOT_CONVERGED;
   });
+  if (rc != SFAIRSC_OK) return rc;
+  if (status != SFAIRSC_OK)
+    g_last_error = "conjugate gradient did not reach rtol (eigenvectors not accurate enough, or a tiny gap)";
+  return status;
 }
 
 }  // extern "C"

@@ -165,6 +165,11 @@ void launch_restart(VecType vt, int n, void* V, int64_t ldv, int m, int K, int B
 // Fill V[:, 0:B] with a seeded pseudo-random block.
 void launch_random_block(VecType vt, int n, void* V, int64_t ldv, int B, uint64_t seed, cudaStream_t s);
 // X64 = V[:, 0:m] Y (Y: m x k row-major, in the basis precision), X64 n x k column-major FP64; V unchanged.
+// thick restart on the tensor cores (FP32 basis, blocks of 4; see restart_tc.cu): whether the
+// shape fits its shared-memory plan, and the launch (Yt: 2 x 8-rounded ldv x 256 floats of scratch)
+bool restart_tc_fits(int n, int64_t ldv, int m, int K, int B);
+void launch_restart_tc(int n, float* V, int64_t ldv, int m, int K, int B, const float* Y, float* Q, const double* E,
+                       float* Yt, int sms, unsigned* err, unsigned long long wait_ns, cudaStream_t s);
 void launch_ritz(VecType vt, int n, const void* V, int64_t ldv, int m, int k, const void* Y, double* X64,
                  cudaStream_t s);
 // partial[b][c] = sum over block b's rows of (AX_c - lam_c X_c)^2.

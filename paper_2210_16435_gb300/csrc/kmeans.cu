@@ -265,7 +265,7 @@ __device__ __forceinline__ unsigned long long mul2_rn(unsigned long long a, unsi
 // compiler): a * 1 is exact, so each rounds a + b once exactly as an add does, but issues on the
 // FMA pipe (plain FP32 adds share a narrower pipe on this GPU).
 template <int DMAX>
-__global__ void assign_kernel(int n, int d, int k, const float* __restrict__ X32, const double* __restrict__ mu,
+__global__ void __launch_bounds__(256, 3) assign_kernel(int n, int d, int k, const float* __restrict__ X32, const double* __restrict__ mu,
                               int* lab, float* dist, unsigned* changed, const int* __restrict__ done, float one) {
   static_assert(DMAX % 2 == 0, "dimension pairs");
   extern __shared__ float msh[];  // k x dp, dp = d rounded up to even, zero padded
@@ -295,33 +295,33 @@ __global__ void assign_kernel(int n, int d, int k, const float* __restrict__ X32
     }
     float best = 0.f;
     int bi = 0;
-    for (int c = 0; c < k; c += 2) {
-      const int c1 = c + 1 < k ? c + 1 : c;
-      const float2* m0 = reinterpret_cast<const float2*>(msh + (size_t)c * dp);
-      const float2* m1 = reinterpret_cast<const float2*>(msh + (size_t)c1 * dp);
-      float a0 = 0.f, a1 = 0.f;
+    // four centroids at a time: four independent chains of adds (each in dimension order) keep the
+    // FMA pipe busy between the dependent adds of one chain
+    for (int c = 0; c < k; c += 4) {
+      const float2* m[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) m[q] = reinterpret_cast<const float2*>(msh + (size_t)min(c + q, k - 1) * dp);
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int j2 = 0; j2 < DMAX / 2; ++j2) {
         if (2 * j2 < d) {
           const unsigned long long xp = pack2(x[2 * j2], x[2 * j2 + 1]);
-          const float2 p0 = m0[j2], p1 = m1[j2];
-          const unsigned long long t0 = sub2_rn(xp, pack2(p0.x, p0.y));
-          const unsigned long long t1 = sub2_rn(xp, pack2(p1.x, p1.y));
-          float s00, s01, s10, s11;
-          unpack2(mul2_rn(t0, t0), s00, s01);
-          unpack2(mul2_rn(t1, t1), s10, s11);
-          a0 = __fmaf_rn(__fmaf_rn(a0, one, s00), one, s01);
-          a1 = __fmaf_rn(__fmaf_rn(a1, one, s10), one, s11);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float2 p = m[q][j2];
+            const unsigned long long t = sub2_rn(xp, pack2(p.x, p.y));
+            float s0, s1;
+            unpack2(mul2_rn(t, t), s0, s1);
+            acc[q] = __fmaf_rn(__fmaf_rn(acc[q], one, s0), one, s1);
+          }
         }
       }
-      if (c == 0 || a0 < best) {
-        best = a0;
-        bi = c;
-      }
-      if (c + 1 < k && a1 < best) {
-        best = a1;
-        bi = c + 1;
-      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (c + q < k && ((c + q) == 0 || acc[q] < best)) {  // first minimum in centroid order
+          best = acc[q];
+          bi = c + q;
+        }
     }
     int* lp = lab + (size_t)r * n + i;
     ch = *lp != bi;
@@ -575,6 +575,9 @@ KmeansResult run_kmeans(int64_t n64, int d, const double* X, int kc, uint64_t se
       } else if (d <= 32) {
         check_cuda(cudaFuncSetAttribute(assign_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)amsmem), "attr");
         assign_kernel<32><<<dim3(nb, R), bs, amsmem, s>>>(n, d, k, X32, mu, lab, dist, changed, done, 1.f);
+      } else if (d <= 56) {
+        check_cuda(cudaFuncSetAttribute(assign_kernel<56>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)amsmem), "attr");
+        assign_kernel<56><<<dim3(nb, R), bs, amsmem, s>>>(n, d, k, X32, mu, lab, dist, changed, done, 1.f);
       } else {
         check_cuda(cudaFuncSetAttribute(assign_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)amsmem), "attr");
         assign_kernel<64><<<dim3(nb, R), bs, amsmem, s>>>(n, d, k, X32, mu, lab, dist, changed, done, 1.f);

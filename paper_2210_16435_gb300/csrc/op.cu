@@ -235,11 +235,10 @@ __device__ void cta_group_sums(int r0, int r1, int h, const uint8_t* __restrict_
         if ((lane & (32 / NA - 1)) == 0 && s0 + j < h) red[warp * P + (s0 + j) * B + v] = acc[0].slot();
       }
     } else {
-      double acc[4][B];
+      constexpr int NA = 4 * B;  // accumulator j * B + v: group s0 + j, vector v
+      double acc[NA];
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int v = 0; v < B; ++v) acc[j][v] = 0.0;
+      for (int q = 0; q < NA; ++q) acc[q] = 0.0;
       for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
         const int g = (int)lab[r] - s0;
         if (g >= 0 && g < 4) {
@@ -249,17 +248,12 @@ __device__ void cta_group_sums(int r0, int r1, int h, const uint8_t* __restrict_
           for (int j = 0; j < 4; ++j)
             if (g == j)
 #pragma unroll
-              for (int v = 0; v < B; ++v) acc[j][v] += x[v];
+              for (int v = 0; v < B; ++v) acc[j * B + v] += x[v];
         }
       }
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int v = 0; v < B; ++v) acc[j][v] = warp_allsum(acc[j][v]);
-      if (lane == 0)
-        for (int j = 0; j < 4 && s0 + j < h; ++j)
-#pragma unroll
-          for (int v = 0; v < B; ++v) red[warp * P + (s0 + j) * B + v] = acc[j][v];
+      reduce_scatter<NA>(acc, lane);
+      const int q = scatter_index<NA>(lane), j = q / B, v = q % B;
+      if ((lane & (32 / NA - 1)) == 0 && s0 + j < h) red[warp * P + (s0 + j) * B + v] = acc[0];
     }
   }
   __syncthreads();
@@ -331,11 +325,10 @@ __device__ void cta_dense_sums(int r0, int r1, int p, const VT* __restrict__ Fd,
         if ((lane & (32 / (4 * B) - 1)) == 0 && s0 + j < p) red[warp * P + (s0 + j) * B + v] = fl[0].slot();
       }
     } else {
-      double acc[4][B];
+      constexpr int NA = 4 * B;
+      double acc[NA];
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int v = 0; v < B; ++v) acc[j][v] = 0.0;
+      for (int q = 0; q < NA; ++q) acc[q] = 0.0;
       for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
         double x[B];
         f(r, x);
@@ -343,17 +336,12 @@ __device__ void cta_dense_sums(int r0, int r1, int p, const VT* __restrict__ Fd,
         for (int j = 0; j < 4; ++j) {
           const double fr = s0 + j < p ? (double)Fd[(size_t)r * p + s0 + j] : 0.0;
 #pragma unroll
-          for (int v = 0; v < B; ++v) acc[j][v] = fma(fr, x[v], acc[j][v]);
+          for (int v = 0; v < B; ++v) acc[j * B + v] = fma(fr, x[v], acc[j * B + v]);
         }
       }
-#pragma unroll
-      for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int v = 0; v < B; ++v) acc[j][v] = warp_allsum(acc[j][v]);
-      if (lane == 0)
-        for (int j = 0; j < 4 && s0 + j < p; ++j)
-#pragma unroll
-          for (int v = 0; v < B; ++v) red[warp * P + (s0 + j) * B + v] = acc[j][v];
+      reduce_scatter<NA>(acc, lane);
+      const int q = scatter_index<NA>(lane), j = q / B, v = q % B;
+      if ((lane & (32 / NA - 1)) == 0 && s0 + j < p) red[warp * P + (s0 + j) * B + v] = acc[0];
     }
   }
   if (lane == 0)
@@ -1031,7 +1019,22 @@ __global__ void __launch_bounds__(256) df_spmv_kernel(int n, const int32_t* __re
         other.lo = __shfl_xor_sync(0xffffffffu, acc[v].lo, o);
         acc[v] = df_add(fa, acc[v], other);
       }
-    if (live && sub == 0) {
+    // every lane of the row holds its sums: lane v of the row forms column v (FP64 is a narrow pipe
+    // on this part, so the row's B FP64 results take one instruction slot, not B)
+    if (Lr >= B) {
+      if (live && sub < B) {
+        float hi = acc[0].hi, lo = acc[0].lo;
+#pragma unroll
+        for (int v = 1; v < B; ++v)
+          if (sub == v) {
+            hi = acc[v].hi;
+            lo = acc[v].lo;
+          }
+        const double s = (double)hi + (double)lo;
+        const double x = X[(size_t)r + (size_t)sub * n];
+        T[(size_t)r + (size_t)sub * n] = normalized ? x - dinv[r] * s : deg[r] * x - s;
+      }
+    } else if (live && sub == 0) {
 #pragma unroll
       for (int v = 0; v < B; ++v) {
         const double s = (double)acc[v].hi + (double)acc[v].lo;

@@ -290,6 +290,12 @@ struct OrthArgs {
 // of U, rsc 16-byte chunks apart, rsc padded so that the lanes of a quarter
 // warp reading different rows fall in different banks.
 constexpr int kWarpBuf = 13312;  // bytes of slice buffer per warp (two slices)
+// the fixed slice geometry: 16 rows, 26 chunks per row (row stride = 2 mod 8 chunks, so the two
+// lanes of each of four consecutive rows in phase A hit distinct bank groups), up to 25 panels + U
+constexpr int kFSR = 16, kFRSC = 26, kFNP = kFRSC - 1, kFSB = kFSR * kFRSC * 16;
+static_assert(2 * kFSB <= kWarpBuf, "two fixed-shape slices fit in a warp's buffer");
+// phase B reads at most chunk kFNP of row 15 of the second slice (lanes past the last panel read chunk 0)
+static_assert(kFSB + (15 * kFRSC + kFNP + 1) * 16 <= kWarpBuf, "phase B reads stay inside the warp's buffer");
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
   const unsigned n = valid ? 16u : 0u;  // src-size 0 fills the 16 bytes with zeros
@@ -352,6 +358,147 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
   if (threadIdx.x == 0) brk = 0;
   __syncthreads();
 
+  // Slice loop with a fixed geometry, for FP32 blocks of 4 against at most kFNP panels (the
+  // common case: a basis of up to 100 columns).  Slices of kFSR = 16 rows, a row stride of
+  // kFRSC = 26 chunks, two lanes per row in phase A and one panel per lane in phase B, all
+  // compile-time, so every shared-memory offset inside a slice is an immediate.  The same
+  // arithmetic in the same order as the general loop.  Lanes whose panel is past np in phase B
+  // accumulate whatever their chunk holds; their sums are never written out.
+  auto fixed_shape = [&](int npp) { return sizeof(VT) == 4 && B == 4 && NC == 1 && npp <= kFNP; };
+  auto fixed_slices = [&](int kind, bool fix, int Jd, int npp, Acc<VT> (&ac)[4][B], Acc<VT> (&gacc)[NA]) {
+   if constexpr (sizeof(VT) == 4 && B == 4 && NC == 1) {
+    const bool upd = kind >= 1, want_c = kind <= 1;
+    const int nsl = (r1 - r0 + kFSR - 1) / kFSR;
+    const int npd = Jd >> 2;                     // panels of the row update (Jd % 4 == 0: blocks of 4)
+    const int pt = fix ? (a.j >> 2) : 0;         // the input block's panel
+    auto fetch_f = [&](int k) {
+      const int sl = warp + kOW * k;
+      if (sl < nsl) {
+        const int rb = r0 + sl * kFSR;
+        const int i = lane & (kFSR - 1);
+        const bool valid = rb + i < r1;
+        const size_t roff = (size_t)(valid ? rb + i : r0) * 4;
+        int c = lane >> 4;
+        unsigned char* d = wbuf + (k & 1) * kFSB + (i * kFRSC + c) * 16;
+        const VT* src = a.V + (size_t)c * pn + roff;
+        for (; c < npp; c += 2, d += 32, src += 2 * pn) cp_async16(d, src, valid);
+        if (c == npp) cp_async16(d, U + roff, valid);
+      }
+      cp_async_commit();
+    };
+    const int ia = lane >> 1, g = lane & 1;  // phase A: row, panel parity
+    fetch_f(0);
+    for (int k = 0; warp + kOW * k < nsl; ++k) {
+      fetch_f(k + 1);
+      cp_async_wait<1>();
+      __syncwarp();
+      const int rb = r0 + (warp + kOW * k) * kFSR;
+      const int rows = min(kFSR, r1 - rb);
+      unsigned char* sb = wbuf + (k & 1) * kFSB;
+      // ---- phase A: d = V[row, 0:Jd] c over this lane's panels g, g + 2, ...; the pair of lanes adds
+      float d[4] = {0.f, 0.f, 0.f, 0.f};
+      if (npd > 0) {
+        float d1[4] = {0.f, 0.f, 0.f, 0.f};
+        const unsigned char* xa = sb + (ia * kFRSC + g) * 16;
+        const float* ca = reinterpret_cast<const float*>(cfs) + g * 16;
+        int pp = g;
+        for (; pp + 2 < npd; pp += 4, xa += 64, ca += 64) {
+          float x0[4], x1[4], c0[16], c1[16];
+          ld4(reinterpret_cast<const float*>(xa), x0);
+          ld4(reinterpret_cast<const float*>(xa + 32), x1);
+          ld_coefs<float, 4>(ca, c0);
+          ld_coefs<float, 4>(ca + 32, c1);
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+              d[v] = fmaf(x0[jj], c0[jj * 4 + v], d[v]);
+              d1[v] = fmaf(x1[jj], c1[jj * 4 + v], d1[v]);
+            }
+        }
+        if (pp < npd) {
+          float x0[4], c0[16];
+          ld4(reinterpret_cast<const float*>(xa), x0);
+          ld_coefs<float, 4>(ca, c0);
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) d[v] = fmaf(x0[jj], c0[jj * 4 + v], d[v]);
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          d[v] += d1[v];
+          d[v] += __shfl_xor_sync(0xffffffffu, d[v], 1);
+        }
+      }
+      if (g == 0 && ia < rows) {
+        if (fix) {  // the input block's row (panel pt, J % 4 == 0), corrected in the slice and in V
+          float* xp = reinterpret_cast<float*>(sb + (ia * kFRSC + pt) * 16);
+          float x[4];
+          ld4(xp, x);
+#pragma unroll
+          for (int v = 0; v < 4; ++v) x[v] -= d[v];
+          st4(xp, x);
+          st4(a.V + (size_t)pt * pn + (size_t)(rb + ia) * 4, x);
+        }
+        float* up = reinterpret_cast<float*>(sb + (ia * kFRSC + npp) * 16);
+        float u[4];
+        ld4(up, u);
+        if (upd) {
+#pragma unroll
+          for (int v = 0; v < 4; ++v) u[v] -= d[v];
+          st4(up, u);
+          st4(U + (size_t)(rb + ia) * 4, u);
+        }
+        if (kind == 0) {
+#pragma unroll
+          for (int v = 0; v < 4; ++v) gacc[v].fma_(u[v], u[v]);
+        } else {
+          int e = 0;
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+#pragma unroll
+            for (int w2 = v; w2 < 4; ++w2) gacc[e++].fma_(u[v], u[w2]);
+        }
+      }
+      __syncwarp();
+      // ---- phase B: lane p (16 or 32 lanes per row) adds V[row, 4p:4p+4]^T u[row] over the slice
+      if (want_c) {
+        auto rowb = [&](const unsigned char* xb, const unsigned char* ub) {
+          float x[4], u[4];
+          ld4(reinterpret_cast<const float*>(xb), x);
+          ld4(reinterpret_cast<const float*>(ub), u);
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) ac[jj][v].fma_(x[jj], u[v]);
+        };
+        if (npp > 16) {
+          const unsigned char* xb = sb + (lane < npp ? lane : 0) * 16;
+          const unsigned char* ub = sb + npp * 16;
+#pragma unroll
+          for (int i = 0; i < kFSR; ++i) rowb(xb + i * kFRSC * 16, ub + i * kFRSC * 16);
+        } else {
+          const int r2 = lane >> 4;
+          const unsigned char* xb = sb + (r2 * kFRSC + ((lane & 15) < npp ? (lane & 15) : 0)) * 16;
+          const unsigned char* ub = sb + (r2 * kFRSC + npp) * 16;
+#pragma unroll
+          for (int i = 0; i < kFSR; i += 2) rowb(xb + i * kFRSC * 16, ub + i * kFRSC * 16);
+        }
+      }
+      if ((k & 3) == 3) {
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) ac[jj][v].flush();
+#pragma unroll
+        for (int e = 0; e < NA; ++e) gacc[e].flush();
+      }
+      __syncwarp();  // the buffer is free for slice k + 2
+    }
+   }
+  };
+
   // sweep kinds: 0 = coefficients + input norms; 1 = update with a.coef, then the
   // next coefficients and the Gram matrix; 2 = update with a.coef, then the Gram matrix.
   // A warp takes the slices r0 + (warp + kOW k) SR, each in two phases:
@@ -374,7 +521,8 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
     const int SR = sh.sr, LPA = sh.lpa, rsc = sh.rsc;
     const int lsr = 31 - __clz(SR);  // SR is a power of two
     const int sbytes = SR * rsc * 16;  // one slice
-    const int LPR = NC == 1 ? lanes_for(np) : 32;
+    // phase B lanes per row: one per panel (the fixed shape: 16 or 32)
+    const int LPR = fixed_shape(np) ? (np > 16 ? 32 : 16) : NC == 1 ? lanes_for(np) : 32;
     const int RPW = 32 / LPR;
     const int p0 = lane & (LPR - 1), ri = lane / LPR;
     const int nsl = (r1 - r0 + SR - 1) / SR;  // slices of this CTA
@@ -408,6 +556,10 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
         for (int v = 0; v < B; ++v) acc[q][jj][v].zero();
 #pragma unroll
     for (int e = 0; e < NA; ++e) ga[e].zero();
+    if (fixed_shape(np)) {
+      if constexpr (sizeof(VT) == 4 && B == 4 && NC == 1)
+        fixed_slices(kind, fix, Jd, np, acc[0], ga);
+    } else {
     fetch(0);
     for (int k = 0; warp + kOW * k < nsl; ++k) {
       fetch(k + 1);
@@ -544,6 +696,7 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
         for (int e = 0; e < NA; ++e) ga[e].flush();
       }
       __syncwarp();  // the buffer is free for slice k + 2
+    }
     }
     cp_async_wait<0>();
     __syncthreads();  // every warp is done with its slices: the buffers take the partials

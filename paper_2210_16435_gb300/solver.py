@@ -30,7 +30,7 @@ class FairSC:
                  prec: str = "mixed", block: int = 1, tol: float = 1e-6, basis: int = 0, max_restarts: int = 200,
                  sigma: float | None = None, seed: int = 1, kmeans_seed: int = 0, kmeans_n_init: int = 1,
                  kmeans_max_iter: int = 100, validate: int = 1, profile: int = 0, wait_limit_us: int = 0,
-                 fault_inject: int = 0, spmv_window: int = 0, orth_mode: int = 0,
+                 fault_inject: int = 0, spmv_window: int = 0, orth_mode: int = 0, restart_mode: int = 0,
                  stream: torch.cuda.Stream | None = None, F: torch.Tensor | None = None):
         if F is not None:
             F = F.to(torch.float64).contiguous()
@@ -55,7 +55,8 @@ class FairSC:
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         opts = B.make_opts(prec, block, tol, basis, max_restarts, sigma, seed, kmeans_seed, kmeans_n_init,
-                           kmeans_max_iter, validate, profile, wait_limit_us, fault_inject, spmv_window, orth_mode)
+                           kmeans_max_iter, validate, profile, wait_limit_us, fault_inject, spmv_window, orth_mode,
+                           restart_mode)
         if F is not None:
             self.ctx = B.sfairsc_create_dense(self.n, self.nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(values),
                                               _DTYPES[values.dtype], _ptr(F), F.shape[1], self.k,

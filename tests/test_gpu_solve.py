@@ -209,3 +209,23 @@ def test_deferred_second_projection(built_lib, prec, block):
     # every launch after a block's first: two sweeps; the start / fresh-block launches may take three
     assert i0["orth_sweeps"] <= 2 * i0["n_orth"] + (i0["restarts"] + 1), i0
     assert i1["orth_sweeps"] >= i0["orth_sweeps"] or i1["matvecs"] != i0["matvecs"]
+
+
+@pytest.mark.parametrize("orth_mode", [0, 1])
+def test_tensor_core_restart(built_lib, orth_mode):
+    """The thick restart on the tensor cores (three-pass TF32, the default for a MIXED basis with blocks
+    of 4) and on the CUDA cores both reach the oracle's pairs, with the same restart counts give or take
+    one; the tensor-core path carries the deferred correction of the last block (orth_mode 0)."""
+    g = configs.msbm_n50k_k20_h5(scale=0.1)["graph"]
+    ref_l, ref_X = smallest_eigenpairs(operator_from_graph(g), 21, tol=1e-13, method="eigsh")
+    d = problem.degrees(g.to_scipy())
+    ref = (ref_l, ref_X / np.sqrt(d)[:, None])
+    l0, _, _, i0 = solve_and_check(g, 20, "mixed", block=4, vdt=torch.float32, ref=ref, orth_mode=orth_mode,
+                                   restart_mode=0)
+    l1, _, _, i1 = solve_and_check(g, 20, "mixed", block=4, vdt=torch.float32, ref=ref, orth_mode=orth_mode,
+                                   restart_mode=1)
+    assert i0["restarts"] > 0 and i0["restarts_tc"] == i0["restarts"], i0
+    assert i1["restarts_tc"] == 0
+    assert abs(i0["restarts"] - i1["restarts"]) <= 1, (i0["restarts"], i1["restarts"])
+    assert i0["dorth_err"] <= 1e-6, i0["dorth_err"]
+    assert eig_rel_err(l0, l1, float(i0["sigma"]), 1e-4) <= 1e-4

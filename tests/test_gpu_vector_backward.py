@@ -98,3 +98,28 @@ def test_vector_gradient_directional_fd_n20k(built_lib):
     eps = 1e-5
     fd = (loss(eps) - loss(-eps)) / (2 * eps)
     assert abs(fd - directional) <= 1e-4 * abs(directional), (fd, directional)
+
+
+def test_vector_backward_status(built_lib):
+    """A MIXED context is refused (its eigenvectors are too rough to deflate with); a conjugate
+    gradient cut short reports NOT_CONVERGED."""
+    from paper_2210_16435_gb300.binding import SFairSCError
+    from paper_2210_16435_gb300.solver import FairSC
+
+    g = graph(400, 4, 3, 30, 8)
+    rp, ci, v, gr = graph_tensors(g)
+    G = torch.randn(g.n, 4, dtype=torch.float64, generator=torch.Generator().manual_seed(1))
+    s = FairSC(rp, ci, v, gr, k=4, h=3, prec="mixed")
+    s.solve(want_labels=False)
+    with pytest.raises(SFairSCError) as e:
+        s.backward_vectors(G)
+    assert e.value.status == -12  # UNSUPPORTED
+    s.close()
+    s = FairSC(rp, ci, v, gr, k=4, h=3, prec="fp64", tol=1e-12)
+    s.solve(want_labels=False)
+    with pytest.raises(SFairSCError) as e:
+        s.backward_vectors(G, max_iter=1)
+    assert e.value.status == -7  # NOT_CONVERGED
+    _, _, it, rr = s.backward_vectors(G)
+    s.close()
+    assert rr <= 1e-10 and it < 1000
