@@ -795,7 +795,7 @@ def run_ours(args):
     if t_orth >= t_op:
         traffic = None
         if args.workload == "msbm_n1m_k50_h10" and args.scale == 1.0 and args.prec == "mixed" and args.block == 4:
-            traffic = recorded_traffic("orth_kernel_traffic_msbm_n1m_k50_h10.md",
+            traffic = recorded_traffic("orth_kernel_msbm_n1m_k50_h10.md",
                                        ["paper_2210_16435_gb300/csrc/orth.cu", "paper_2210_16435_gb300/csrc/common.cuh"])
         roof = {"kernel": "orth_kernel (CGS2 + CholQR)", "bound": "hbm", "achieved": orth_gbs, "peak": peak,
                 "unit": "GB/s", "frac": orth_gbs / peak, "traffic": traffic,
