@@ -411,19 +411,24 @@ __global__ void __launch_bounds__(256) diagnostics_kernel(int n, int k, int h, c
     pj[q] = p < npairs ? i + rem : -1;
   }
   __syncthreads();
+  __shared__ double sqd[64];  // sqrt(d_r) of the tile's rows: one FP64 root per row, not per entry
+  __shared__ int labs[64];
   for (int t0 = blockIdx.x * 64; t0 < n; t0 += gridDim.x * 64) {
     const int rows = min(64, n - t0);
+    if (threadIdx.x < 64) {
+      const int r = t0 + threadIdx.x;
+      sqd[threadIdx.x] = (int)threadIdx.x < rows ? sqrt(deg[r]) : 0.0;
+      labs[threadIdx.x] = (int)threadIdx.x < rows ? (int)lab[r] : 0;
+    }
+    __syncthreads();
     for (int e = threadIdx.x; e < 64 * k; e += blockDim.x) {
       const int rr = e / k, c = e % k;
-      double v = 0.0;
-      if (rr < rows) {
-        const int r = t0 + rr;
-        const double hv = H[(size_t)r * k + c];
-        v = hv * sqrt(deg[r]);
-        atomicAdd(&gs[lab[r] * k + c], hv);
-      }
+      const double v = rr < rows ? H[(size_t)(t0 + rr) * k + c] * sqd[rr] : 0.0;
       Xs[rr * ks + c] = (AT)v;
     }
+    // F^T H group sums: thread c owns column c (no atomics; rows in order, so reproducible)
+    if ((int)threadIdx.x < k)
+      for (int rr = 0; rr < rows; ++rr) gs[labs[rr] * k + threadIdx.x] += H[(size_t)(t0 + rr) * k + threadIdx.x];
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < MP; ++q) {
