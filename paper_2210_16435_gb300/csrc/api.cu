@@ -339,6 +339,7 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   }
   P[kPSigma] = c->sigma;
   for (int a = 0; a + 1 < h; ++a) P[kPLinv + a] = 1.0 / P[kPL + a * kLStride + a];
+  fill_group_map(P, h, dense);
   c->params = c->dalloc<double>(kParams);
   check_cuda(cudaMemcpyAsync(c->params, P, sizeof(double) * kParams, cudaMemcpyHostToDevice, s), "h2d");
 

@@ -18,7 +18,8 @@ constexpr int kPL = 32;                // lower Cholesky factor of C^T C, row-ma
 constexpr int kLStride = 31;
 constexpr int kPSigma = kPL + 31 * 31; // sigma
 constexpr int kPLinv = kPSigma + 1;    // reciprocals of the factor's diagonal, 31 entries
-constexpr int kParams = 1056;
+constexpr int kPG = 1056;               // h x h map from the group sums to the correction coefficients
+constexpr int kParams = kPG + 32 * 32;
 
 enum class VecType { F64 = 0, F32 = 1 };
 
@@ -107,6 +108,10 @@ void launch_df_spmv(int n, const int32_t* row_ptr, const int32_t* col, const voi
 // Largest co-resident grid of the operator kernel for this instantiation.
 int operator_max_grid(VecType vt, int val_dtype, int nvec, int threads, size_t smem);
 size_t operator_smem_bytes(int threads, int h, int nvec, VecType vt);
+// The linear map tot -> coef of the operator's small solve ((C^T C)^{-1} and, for group labels, the
+// shift by z), as an h x h row-major matrix at P[kPG], from z, the Cholesky factor and its inverse
+// diagonal already in P: the kernels then form every coefficient in parallel.
+void fill_group_map(double* P, int h, bool dense);
 
 // Setup kernels.
 void launch_validate(int n, int64_t nnz, const int32_t* row_ptr, const int32_t* col, const void* val, int val_dtype,

@@ -134,40 +134,17 @@ __device__ __forceinline__ void reduce_partials(const double* partial, int nctas
   __syncthreads();
 }
 
-// From the group sums tot[s*B+v] (s < h) of D^{-1/2} x, solve
-// (C^T C) a = C^T x for every vector and return the per-group correction
-// coef[s*B+v] = a'_s - z.a so that (C a)_i = d_i^{-1/2} coef[g_i].
-// Also returns a itself (for the shift term).  Threads v < B work.
+// coef = G tot for every (group, vector) in parallel (G precomputed on the host from the Cholesky
+// factor of C^T C: the same small solve for every right-hand side), zero past h groups.
 template <int B>
-__device__ __forceinline__ void solve_groups(const double* tot, const double* params, int h, double* a_out,
-                                             double* coef, bool dense = false) {
-  const int v = threadIdx.x;
-  if (v < B) {
-    const int p = h - 1;
-    double sum = 0.0;
-    if (!dense)
-      for (int s = 0; s < h; ++s) sum += tot[s * B + v];
-    double y[kMaxGroups];
-    // forward: L y = rhs, rhs_s = tot_s - z_s * sum (labels) or tot_s (dense F: tot = C^T x)
-    for (int s = 0; s < p; ++s) {
-      double r = tot[s * B + v] - (dense ? 0.0 : params[kPZ + s] * sum);
-      for (int q = 0; q < s; ++q) r -= params[kPL + s * kLStride + q] * y[q];
-      y[s] = r * params[kPLinv + s];
+__device__ __forceinline__ void apply_group_map(const double* G, const double* tot, int h, double* coef) {
+  for (int i = threadIdx.x; i < kMaxGroups * B; i += blockDim.x) {
+    double c = 0.0;
+    if (i < h * B) {
+      const int s = i / B, v = i % B;
+      for (int t = 0; t < h; ++t) c = fma(G[s * h + t], tot[t * B + v], c);
     }
-    // backward: L^T a = y
-    for (int s = p - 1; s >= 0; --s) {
-      double r = y[s];
-      for (int q = s + 1; q < p; ++q) r -= params[kPL + q * kLStride + s] * y[q];
-      y[s] = r * params[kPLinv + s];
-    }
-    double za = 0.0;
-    if (!dense)
-      for (int s = 0; s < p; ++s) za += params[kPZ + s] * y[s];
-    for (int s = 0; s < p; ++s) {
-      a_out[s * B + v] = y[s];
-      coef[s * B + v] = y[s] - za;  // labels: (C a)_i = d_i^{-1/2} coef[g_i]; dense: coef = a
-    }
-    coef[p * B + v] = -za;
+    coef[i] = c;
   }
   __syncthreads();
 }
@@ -374,7 +351,10 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
   double* avec = tot + kMaxGroups * B;                 // 32*B
   double* coefA = avec + kMaxGroups * B;               // 32*B
   double* coefD = coefA + kMaxGroups * B;              // 32*B
-  VT* coefAv = reinterpret_cast<VT*>(coefD + kMaxGroups * B);  // 32*B, in the vector type
+  double* Gs = coefD + kMaxGroups * B;                 // h x h: group sums -> correction coefficients
+  VT* coefAv = reinterpret_cast<VT*>(Gs + h * h);      // 32*B, in the vector type
+  (void)avec;
+  for (int i = threadIdx.x; i < h * h; i += blockDim.x) Gs[i] = a.params[kPG + i];  // synced before use
 
   const int r0 = a.cta_rows[blockIdx.x], r1 = a.cta_rows[blockIdx.x + 1];
   if (a.stall && !wait_flag(a.stall, a.err, a.wait_ns)) return;
@@ -414,7 +394,7 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
     if (!grid_sync(a.bar, a.err, a.wait_ns)) return;
     // ---------------- phase B: a = (C^T C)^{-1} C^T w
     reduce_partials(a.partial, gridDim.x, P, scratch, tot);
-    solve_groups<B>(tot, a.params, h, avec, coefA, dense);
+    apply_group_map<B>(Gs, tot, h, coefA);
   } else {
     for (int i = threadIdx.x; i < kMaxGroups * B; i += blockDim.x) {
       coefA[i] = 0.0;
@@ -712,24 +692,17 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
   // ---------------- phase D: b = (C^T C)^{-1} C^T t; out = t - C (b - sigma a)
   reduce_partials(a.partial, gridDim.x, P, scratch, tot);
   {
-    // reuse solve_groups on tot, then fold in -sigma a
-    double* bvec = scratch;  // scratch is free now (reduce_partials synced)
-    solve_groups<B>(tot, a.params, h, bvec, coefD, dense);
+    // C u with u = b - sigma a is linear in the sums: coefD = G C^T t - sigma coefA
     const double sigma = a.params[kPSigma];
-    if (threadIdx.x < B) {
-      const int v = threadIdx.x;
-      const int p = h - 1;
-      double zu = 0.0;
-      for (int s = 0; s < p; ++s) {
-        const double u = bvec[s * B + v] - sigma * avec[s * B + v];
-        if (!dense) zu += a.params[kPZ + s] * u;
-        coefD[s * B + v] = u;
+    for (int i = threadIdx.x; i < kMaxGroups * B; i += blockDim.x) {
+      double cd = 0.0;
+      if (i < P) {
+        const int s2 = i / B, v = i % B;
+        for (int t = 0; t < h; ++t) cd = fma(Gs[s2 * h + t], tot[t * B + v], cd);
+        cd -= sigma * coefA[i];
       }
-      for (int s = 0; s < p; ++s) coefD[s * B + v] -= zu;
-      coefD[p * B + v] = -zu;
+      coefAv[i] = (VT)cd;
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < kMaxGroups * B; i += blockDim.x) coefAv[i] = (VT)coefD[i];
     __syncthreads();
   }
 #pragma unroll 4
@@ -749,7 +722,8 @@ size_t operator_smem_bytes(int threads, int h, int nvec, VecType vt) {
   const int nwarps = threads / 32;
   const size_t vs = vt == VecType::F64 ? 8 : 4;
   const int P = h * nvec;
-  return sizeof(double) * ((size_t)nwarps * P + threads + P + 4 * kMaxGroups * nvec) + vs * kMaxGroups * nvec + 64;
+  return sizeof(double) * ((size_t)nwarps * P + threads + P + 4 * kMaxGroups * nvec + (size_t)h * h) +
+         vs * kMaxGroups * nvec + 64;
 }
 
 template <typename VT, typename MT, int B>

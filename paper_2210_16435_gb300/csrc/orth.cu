@@ -861,8 +861,30 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
     // The operator saw the input block before its correction: A q = A q_stored - A V[:, 0:j] e, and
     // V^T A V[:, 0:j] e = H[0:J, 0:j] e, so the recorded coefficients drop that term.  (The
     // projected vector itself is unchanged: U - V c1 removes everything in span(V) either way.)
-    if (a.j >= 0)
-      for (int p = blockIdx.x; p < P; p += gridDim.x) {
+    // one thread per owned coefficient (the correction below is a j-term FP64 dot product, and
+    // FP64 is a narrow pipe: done by every thread of the CTA it cost more than a sweep); its
+    // operands are first staged in shared memory by the whole CTA, one round trip instead of j
+    const int Qown = P > (int)blockIdx.x ? (P - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+    const bool staged = a.j > 0 && a.pend_in != nullptr && a.j * B + Qown * a.j <= kOW * kRed;
+    if (staged) {
+      double* pe = red;              // pend_in, j x B
+      double* hr = red + a.j * B;    // the owned rows of H[:, 0:j]
+      for (int i = threadIdx.x; i < a.j * B; i += blockDim.x) pe[i] = __ldcg(a.pend_in + i);
+      for (int i = threadIdx.x; i < Qown * a.j; i += blockDim.x) {
+        const int q = i / a.j, c = i % a.j;
+        hr[i] = hfull((int)(blockIdx.x + gridDim.x * q) / B, c);
+      }
+      __syncthreads();
+      for (int q = threadIdx.x; q < Qown; q += blockDim.x) {
+        const int p = blockIdx.x + gridDim.x * q, v = p % B;
+        double t = 0.0;
+        for (int c = 0; c < a.j; ++c) t = fma(hr[q * a.j + c], pe[c * B + v], t);
+        a.H[(size_t)(p / B) + (size_t)a.ldh * (a.j + v)] = a.coef[p] - t;
+      }
+      __syncthreads();
+    }
+    if (a.j >= 0 && !staged)
+      for (int p = blockIdx.x + gridDim.x * threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
         double hv = a.coef[p];
         if (a.pend_in) {
           const int r = p / B, v = p % B;
@@ -890,12 +912,16 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
       // the Gram matrix of the projected block is G - c2^T c2 (V^T V = I, V^T U = c2)
       reduce_owned(a.partial, kStride, gridDim.x, P, a.coef, scratch);
       if (a.j >= 0)
-        for (int p = blockIdx.x; p < P; p += gridDim.x) a.H[(size_t)(p / B) + (size_t)a.ldh * (a.j + p % B)] += a.coef[p];
+        for (int p = blockIdx.x + gridDim.x * threadIdx.x; p < P; p += gridDim.x * blockDim.x)
+          a.H[(size_t)(p / B) + (size_t)a.ldh * (a.j + p % B)] += a.coef[p];
       if (!grid_sync(a.bar, a.err, a.wait_ns)) return;
+      // c2 staged in shared memory by all threads (one round trip), then the B x B products
+      for (int i = threadIdx.x; i < P; i += blockDim.x) red[i] = __ldcg(a.coef + i);
+      __syncthreads();
       if ((int)threadIdx.x < B * B) {
         const int v = threadIdx.x / B, w2 = threadIdx.x % B;
         double t = 0.0;
-        for (int c = 0; c < J; ++c) t = fma(__ldcg(a.coef + c * B + v), __ldcg(a.coef + c * B + w2), t);
+        for (int c = 0; c < J; ++c) t = fma(red[c * B + v], red[c * B + w2], t);
         scratch[threadIdx.x] = t;
       }
       __syncthreads();
@@ -904,7 +930,8 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
     } else if (again) {
       reduce_owned(a.partial, kStride, gridDim.x, P, a.coef, scratch);
       if (a.j >= 0)
-        for (int p = blockIdx.x; p < P; p += gridDim.x) a.H[(size_t)(p / B) + (size_t)a.ldh * (a.j + p % B)] += a.coef[p];
+        for (int p = blockIdx.x + gridDim.x * threadIdx.x; p < P; p += gridDim.x * blockDim.x)
+          a.H[(size_t)(p / B) + (size_t)a.ldh * (a.j + p % B)] += a.coef[p];
       if (!grid_sync(a.bar, a.err, a.wait_ns)) return;
       // sweep 3: U -= V c2; Gram
       if (!sweep(2)) return;

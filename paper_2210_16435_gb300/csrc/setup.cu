@@ -5,6 +5,9 @@
 // cooperative kernels share.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -301,6 +304,33 @@ __global__ void f64_to_f32_rows_kernel(int64_t count, const double* in, float* o
 void launch_f64_to_f32(int64_t count, const double* in, float* out, cudaStream_t s) {
   f64_to_f32_rows_kernel<<<1024, 256, 0, s>>>(count, in, out);
   check_cuda(cudaGetLastError(), "conversion launch");
+}
+
+
+// The small solve of the operator applied to each unit vector: column t of the map is the
+// coefficient vector of tot = e_t (forward and backward substitution with the factor L of C^T C,
+// then, for labels, the shift by z . y that expresses C a through the group coefficients).
+void fill_group_map(double* P, int h, bool dense) {
+  const int p = h - 1;
+  std::vector<double> y((size_t)std::max(p, 1));
+  for (int t = 0; t < h; ++t) {
+    const double sum = dense ? 0.0 : 1.0;  // sum of the unit vector's entries
+    for (int s = 0; s < p; ++s) {
+      double r = (s == t ? 1.0 : 0.0) - (dense ? 0.0 : P[kPZ + s] * sum);
+      for (int q = 0; q < s; ++q) r -= P[kPL + s * kLStride + q] * y[q];
+      y[s] = r * P[kPLinv + s];
+    }
+    for (int s = p - 1; s >= 0; --s) {
+      double r = y[s];
+      for (int q = s + 1; q < p; ++q) r -= P[kPL + q * kLStride + s] * y[q];
+      y[s] = r * P[kPLinv + s];
+    }
+    double za = 0.0;
+    if (!dense)
+      for (int s = 0; s < p; ++s) za += P[kPZ + s] * y[s];
+    for (int s = 0; s < p; ++s) P[kPG + s * h + t] = y[s] - za;
+    P[kPG + p * h + t] = -za;
+  }
 }
 
 }  // namespace sfairsc

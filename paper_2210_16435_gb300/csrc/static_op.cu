@@ -152,6 +152,7 @@ static int apply_static(int64_t n64, int64_t nnz, const int32_t* row_ptr, const 
   for (int b = 0; b < (n + 255) / 256; ++b) sigma = std::max(sigma, g_host_blockmax[b]);
   P[kPSigma] = sigma;
   for (int a = 0; a + 1 < h; ++a) P[kPLinv + a] = 1.0 / P[kPL + a * kLStride + a];
+  fill_group_map(P, h, false);
   check_cuda(cudaMemcpyAsync(S->params, P, sizeof(double) * kParams, cudaMemcpyHostToDevice, s), "h2d");
 
   // the fused operator, on the static scratch
