@@ -427,6 +427,20 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
     }
     c->op64.Fd = c->Fd64;
   }
+  // K (C^T t from the projected input, before the SpMV): the operator then writes its rows in
+  // final form with two grid barriers fewer
+  if (h > 1) {
+    const int kpad = (h + 3) & ~3;
+    double* K64 = c->dalloc<double>((size_t)n * kpad);
+    float* K32 = c->vt == VecType::F32 ? c->dalloc<float>((size_t)n * kpad) : nullptr;
+    launch_kmat(n, c->row_ptr, c->col, c->val_orig, c->vdt_orig, c->lab, dense ? c->Fd64 : nullptr,
+                dense ? h - 1 : 0, h, c->dinv64, c->deg, c->normalized, K64, K32, s);
+    double* part2 = c->dalloc<double>((size_t)grid * (kMaxGroups + 1) * 4);
+    c->op.Kp = K32 ? (const void*)K32 : (const void*)K64;
+    c->op.partial2 = part2;
+    c->op64.Kp = K64;
+    c->op64.partial2 = part2;
+  }
   c->proj64 = c->op64;
   c->proj64.mode = 1;
   // shared-memory windows of the SpMV input, one table per block size, for both precisions

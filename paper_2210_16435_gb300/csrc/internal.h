@@ -85,6 +85,10 @@ struct OpPlan {
   const unsigned* stall_flag = nullptr;  // non-null: the launch first waits for this word (never set) to become nonzero
   WindowTable win[3];  // by block size b = 1, 2, 4 (index 0, 1, 2)
   const void* Fd = nullptr;  // dense constraints F (n x (h - 1), row-major, vector type) instead of labels
+  // C^T t from y (vector type, n x kpad in 4-column panels, kpad = h rounded up to 4) and the
+  // per-CTA sums it needs (grid x 33 x 4 doubles); nullptr: a pass over t after the SpMV
+  const void* Kp = nullptr;
+  double* partial2 = nullptr;
 };
 
 // Rows of ytil (b values of vs bytes) a window may hold next to the kernel's other shared memory.
@@ -112,6 +116,12 @@ size_t operator_smem_bytes(int threads, int h, int nvec, VecType vt);
 // shift by z), as an h x h row-major matrix at P[kPG], from z, the Cholesky factor and its inverse
 // diagonal already in P: the kernels then form every coefficient in parallel.
 void fill_group_map(double* P, int h, bool dense);
+// K_c = d_c^{-1/2} (F_c - sum_r w_cr F_r / d_r) (normalized) or d_c F_c - sum_r w_cr F_r, row c of the
+// n x kpad matrix in 4-column panels (zero past the constraint columns), in FP64 and FP32 (either
+// output may be null); F is the group indicator (Fd = nullptr) or the dense F (n x p, row-major).
+void launch_kmat(int n, const int32_t* row_ptr, const int32_t* col, const void* val, int val_dtype, const uint8_t* lab,
+                 const double* Fd, int p, int h, const double* dinv64, const double* deg, int normalized,
+                 double* K64, float* K32, cudaStream_t s);
 
 // Setup kernels.
 void launch_validate(int n, int64_t nnz, const int32_t* row_ptr, const int32_t* col, const void* val, int val_dtype,

@@ -355,20 +355,37 @@ __global__ void update_sums_kernel(int n, int d, int k, const float* __restrict_
   };
   int cur = -1;
   long long a0 = 0, a1 = 0, cnt = 0;
-  for (long long i = w0; i < min((long long)n, w0 + rows_per_warp); ++i) {
-    const int l = lb[i];
-    if (l != cur) {
-      if (cur >= 0) {
-        if (lane < d) atomicAdd((unsigned long long*)&ssum[cur * d + lane], (unsigned long long)a0);
-        if (lane + 32 < d) atomicAdd((unsigned long long*)&ssum[cur * d + lane + 32], (unsigned long long)a1);
-        if (lane == 0) atomicAdd((unsigned long long*)&ssum[k * d + cur], (unsigned long long)cnt);
-      }
-      cur = l;
-      a0 = a1 = cnt = 0;
+  const long long wend = min((long long)n, w0 + rows_per_warp);
+  // eight rows' labels and coordinates in flight before they are added (integer sums: the order
+  // of the adds does not change the result)
+  constexpr int RF = 8;
+  for (long long i0 = w0; i0 < wend; i0 += RF) {
+    int l[RF];
+    float x0[RF], x1[RF];
+#pragma unroll
+    for (int q = 0; q < RF; ++q) {
+      const long long i = i0 + q;
+      const bool in = i < wend;
+      l[q] = in ? lb[i] : -1;
+      x0[q] = in && lane < d ? X32[(size_t)i * d + lane] : 0.f;
+      x1[q] = in && lane + 32 < d ? X32[(size_t)i * d + lane + 32] : 0.f;
     }
-    if (lane < d) a0 += quant(X32[(size_t)i * d + lane]);
-    if (lane + 32 < d) a1 += quant(X32[(size_t)i * d + lane + 32]);
-    cnt += 1;
+#pragma unroll
+    for (int q = 0; q < RF; ++q) {
+      if (l[q] < 0) break;
+      if (l[q] != cur) {
+        if (cur >= 0) {
+          if (lane < d) atomicAdd((unsigned long long*)&ssum[cur * d + lane], (unsigned long long)a0);
+          if (lane + 32 < d) atomicAdd((unsigned long long*)&ssum[cur * d + lane + 32], (unsigned long long)a1);
+          if (lane == 0) atomicAdd((unsigned long long*)&ssum[k * d + cur], (unsigned long long)cnt);
+        }
+        cur = l[q];
+        a0 = a1 = cnt = 0;
+      }
+      if (lane < d) a0 += quant(x0[q]);
+      if (lane + 32 < d) a1 += quant(x1[q]);
+      cnt += 1;
+    }
   }
   if (cur >= 0) {
     if (lane < d) atomicAdd((unsigned long long*)&ssum[cur * d + lane], (unsigned long long)a0);

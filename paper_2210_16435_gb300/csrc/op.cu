@@ -55,6 +55,11 @@ struct OpArgs {
   // dense constraints: F (n x fp, row-major, in the vector type) replaces the group labels
   const VT* __restrict__ Fd;
   int fp;
+  // C^T t from the projected input: K (n x kpad in 4-column panels, kpad = h rounded up to 4) with
+  // C^T t = sum_c y_c K_c; nullptr: the group sums of t in a pass of their own after the SpMV
+  const VT* __restrict__ Kp;
+  int kpad;
+  double* partial2;  // per-CTA sums y^T K (grid x (kpad + 1) x B)
 };
 
 template <typename VT, int B>
@@ -132,6 +137,18 @@ __device__ __forceinline__ void reduce_partials(const double* partial, int nctas
     out[t] = s;
   }
   __syncthreads();
+}
+
+// Four consecutive values (16 or 32 bytes, aligned).
+template <typename VT>
+__device__ __forceinline__ void ld_row4(const VT* p, VT (&x)[4]) {
+  if constexpr (sizeof(VT) == 4) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+  } else {
+    const double2 u = reinterpret_cast<const double2*>(p)[0], v = reinterpret_cast<const double2*>(p)[1];
+    x[0] = u.x; x[1] = u.y; x[2] = v.x; x[3] = v.y;
+  }
 }
 
 // coef = G tot for every (group, vector) in parallel (G precomputed on the host from the Cholesky
@@ -252,8 +269,8 @@ __device__ void cta_group_sums(int r0, int r1, int h, const uint8_t* __restrict_
 // the scaling folded into f): partial[blockIdx.x][s * B + v] = sum_r F[r][s] f(r)_v
 // for s < p, zero in the slot s = p.  Thread per row, four columns per pass;
 // the same FP32 windows and TwoSum carries as the group sums, fixed order.
-template <typename VT, int B, typename Fn>
-__device__ void cta_dense_sums(int r0, int r1, int p, const VT* __restrict__ Fd, double* red, double* partial, Fn&& f) {
+template <typename VT, int B, typename FL, typename Fn>
+__device__ void cta_dense_sums(int r0, int r1, int p, FL&& fload, double* red, double* partial, Fn&& f) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int h = p + 1, P = h * B;
   for (int s0 = 0; s0 < p; s0 += 4) {
@@ -271,8 +288,7 @@ __device__ void cta_dense_sums(int r0, int r1, int p, const VT* __restrict__ Fd,
       for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
         float x[B], fr[4];
         f(r, x);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) fr[j] = s0 + j < p ? Fd[(size_t)r * p + s0 + j] : 0.f;
+        fload(r, s0, fr);
 #pragma unroll
         for (int j = 0; j < 4; ++j)
 #pragma unroll
@@ -307,14 +323,13 @@ __device__ void cta_dense_sums(int r0, int r1, int p, const VT* __restrict__ Fd,
 #pragma unroll
       for (int q = 0; q < NA; ++q) acc[q] = 0.0;
       for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-        double x[B];
+        double x[B], fr[4];
         f(r, x);
+        fload(r, s0, fr);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const double fr = s0 + j < p ? (double)Fd[(size_t)r * p + s0 + j] : 0.0;
+        for (int j = 0; j < 4; ++j)
 #pragma unroll
-          for (int v = 0; v < B; ++v) acc[j * B + v] = fma(fr, x[v], acc[j * B + v]);
-        }
+          for (int v = 0; v < B; ++v) acc[j * B + v] = fma(fr[j], x[v], acc[j * B + v]);
       }
       reduce_scatter<NA>(acc, lane);
       const int q = scatter_index<NA>(lane), j = q / B, v = q % B;
@@ -345,14 +360,19 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
   const int P = h * B;
   const bool grouped = h > 1;
   // shared layout
-  double* red = reinterpret_cast<double*>(smem_raw);  // nwarps * P
-  double* scratch = red + nwarps * P;                  // blockDim.x (+P)
-  double* tot = scratch + blockDim.x + P;              // P
-  double* avec = tot + kMaxGroups * B;                 // 32*B
+  const int Pr = ((((h + 3) & ~3)) + 1) * B;            // widest per-warp row: group sums or y^T K
+  double* red = reinterpret_cast<double*>(smem_raw);  // nwarps * Pr
+  double* scratch = red + nwarps * Pr;                 // blockDim.x (+Pr)
+  double* tot = scratch + blockDim.x + Pr;             // (32 + 1) * B
+  double* avec = tot + (kMaxGroups + 1) * B;           // 32*B
   double* coefA = avec + kMaxGroups * B;               // 32*B
   double* coefD = coefA + kMaxGroups * B;              // 32*B
   double* Gs = coefD + kMaxGroups * B;                 // h x h: group sums -> correction coefficients
   VT* coefAv = reinterpret_cast<VT*>(Gs + h * h);      // 32*B, in the vector type
+  VT* coefDv = coefAv + kMaxGroups * B;                // 32*B, in the vector type
+  // (rows of the input contiguous: the extra pass re-reads them, which strided columns make dearer
+  // than the pass it saves)
+  const bool fusedD = a.Kp != nullptr && grouped && a.mode == 0 && (B == 1 || (a.wcs == 1 && a.wrs == B));
   (void)avec;
   for (int i = threadIdx.x; i < h * h; i += blockDim.x) Gs[i] = a.params[kPG + i];  // synced before use
 
@@ -379,7 +399,14 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
     }
   };
   auto group_sums = [&](auto&& f) {
-    if (dense) cta_dense_sums<VT, B>(r0, r1, a.fp, a.Fd, red, a.partial, f);
+    if (dense)
+      cta_dense_sums<VT, B>(
+          r0, r1, a.fp,
+          [&](int r, int s0, VT(&fr)[4]) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) fr[j] = s0 + j < a.fp ? a.Fd[(size_t)r * a.fp + s0 + j] : VT(0);
+          },
+          red, a.partial, f);
     else cta_group_sums<VT, B>(r0, r1, h, a.lab, red, a.partial, f);
   };
 
@@ -425,8 +452,41 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
       a.ytil[(size_t)r * B + v] = a.normalized ? sc * y : y;
     }
   }
+  if (fusedD) {
+    // C^T t = sum_c y_c K_c with K_c = d_c^{-1/2} (F_c - sum_r w_rc F_r / d_r) (normalized) or
+    // d_c F_c - sum_r w_rc F_r (not): t = L_n y summed against C by the symmetry of W, so the
+    // correction is known before the SpMV and its rows can be written in final form
+    const size_t pn = (size_t)a.n * 4;
+    cta_dense_sums<VT, B>(
+        r0, r1, a.kpad,
+        [&](int r, int s0, VT(&fr)[4]) { ld_row4<VT>(a.Kp + (size_t)(s0 >> 2) * pn + (size_t)r * 4, fr); },
+        red, a.partial2, [&](int r, VT(&x)[B]) {
+          const VT sc = scale(r);
+          VT cr[B];
+          load_strided<VT, B>(a.w, r, a.wrs, a.wcs, x);
+          corr(r, coefAv, cr);
+#pragma unroll
+          for (int v = 0; v < B; ++v) x[v] -= sc * cr[v];
+        });
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) *a.work = 0u;  // no CTA takes a row block before the barrier
   if (!grid_sync(a.bar, a.err, a.wait_ns)) return;
+  if (fusedD) {
+    const int P2 = (a.kpad + 1) * B;
+    reduce_partials(a.partial2, gridDim.x, P2, scratch, tot);
+    // C u with u = b - sigma a: coefD = G C^T t - sigma coefA
+    const double sigma = a.params[kPSigma];
+    for (int i = threadIdx.x; i < kMaxGroups * B; i += blockDim.x) {
+      double cd = 0.0;
+      if (i < P) {
+        const int s2 = i / B, v = i % B;
+        for (int t = 0; t < h; ++t) cd = fma(Gs[s2 * h + t], tot[t * B + v], cd);
+        cd -= sigma * coefA[i];
+      }
+      coefDv[i] = (VT)cd;
+    }
+    __syncthreads();
+  }
 
   // ---------------- phase C (no windows): t = L_n y, written to out
   // Warps take blocks of 4 row groups from a global counter (load balance
@@ -528,13 +588,15 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
         const VT sc = scale(r);
         VT dd = VT(1);
         if (!a.normalized) dd = (VT)a.deg[r];
-        VT wr[B], cr[B];
+        VT wr[B], cr[B], cd[B];
         load_strided<VT, B>(a.w, r, a.wrs, a.wcs, wr);
         corr(r, coefAv, cr);
+        if (fusedD) corr(r, coefDv, cd);
 #pragma unroll
         for (int v = 0; v < B; ++v) {
           const VT y = wr[v] - sc * cr[v];
-          a.out[r * a.ors + v * a.ocs] = a.normalized ? y - sc * sacc[v] : dd * y - sacc[v];
+          const VT t = a.normalized ? y - sc * sacc[v] : dd * y - sacc[v];
+          a.out[r * a.ors + v * a.ocs] = fusedD ? t - sc * cd[v] : t;
         }
       }
 #pragma unroll
@@ -652,13 +714,15 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
           const VT sc = scale(r);
           VT dd = VT(1);
           if (!a.normalized) dd = (VT)a.deg[r];
-          VT wr[B], cr[B];
+          VT wr[B], cr[B], cd[B];
           load_strided<VT, B>(a.w, r, a.wrs, a.wcs, wr);
           corr(r, coefAv, cr);
+          if (fusedD) corr(r, coefDv, cd);
 #pragma unroll
           for (int v = 0; v < B; ++v) {
             const VT y = wr[v] - sc * cr[v];
-            a.out[r * a.ors + v * a.ocs] = a.normalized ? y - sc * sacc[v] : dd * y - sacc[v];
+            const VT t = a.normalized ? y - sc * sacc[v] : dd * y - sacc[v];
+            a.out[r * a.ors + v * a.ocs] = fusedD ? t - sc * cd[v] : t;
           }
         }
 #pragma unroll
@@ -673,7 +737,7 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
       }
     }
   }
-  if (!grouped) return;
+  if (!grouped || fusedD) return;
   // t rows were written by any CTA: make them visible, then group sums over own rows (through L2)
   if (!grid_sync(a.bar, a.err, a.wait_ns)) return;
   group_sums([&](int r, VT(&x)[B]) {
@@ -721,9 +785,9 @@ __global__ void __launch_bounds__(1024, 1) fused_operator_kernel(OpArgs<VT, MT> 
 size_t operator_smem_bytes(int threads, int h, int nvec, VecType vt) {
   const int nwarps = threads / 32;
   const size_t vs = vt == VecType::F64 ? 8 : 4;
-  const int P = h * nvec;
-  return sizeof(double) * ((size_t)nwarps * P + threads + P + 4 * kMaxGroups * nvec + (size_t)h * h) +
-         vs * kMaxGroups * nvec + 64;
+  const int Pr = (((h + 3) & ~3) + 1) * nvec;
+  return sizeof(double) * ((size_t)nwarps * Pr + threads + Pr + (4 * kMaxGroups + 1) * nvec + (size_t)h * h) +
+         2 * vs * kMaxGroups * nvec + 64;
 }
 
 template <typename VT, typename MT, int B>
@@ -767,6 +831,9 @@ static void launch_t(const OpPlan& p, const void* w, int64_t wrs, int64_t wcs, v
   a.win_off = (int)((base + 15) / 16 * 16);
   a.Fd = static_cast<const VT*>(p.Fd);
   a.fp = p.Fd ? p.h - 1 : 0;
+  a.Kp = static_cast<const VT*>(p.Kp);
+  a.kpad = (p.h + 3) & ~3;
+  a.partial2 = p.partial2;
   const size_t smem = (size_t)a.win_off + (windows ? (size_t)wt.win_rows * B * sizeof(VT) : 0);
   auto kern = fused_operator_kernel<VT, MT, B>;
   check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "operator smem attr");

@@ -333,4 +333,55 @@ void fill_group_map(double* P, int h, bool dense) {
   }
 }
 
+
+template <typename MT>
+__global__ void kmat_kernel(int n, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                            const MT* __restrict__ val, const uint8_t* __restrict__ lab, const double* __restrict__ Fd,
+                            int p, int kpad, const double* __restrict__ dinv, const double* __restrict__ deg,
+                            int normalized, double* K64, float* K32) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  double M[kMaxGroups];
+  for (int t = 0; t < kpad; ++t) M[t] = 0.0;
+  for (int e = row_ptr[c]; e < row_ptr[c + 1]; ++e) {
+    const int r = col[e];
+    const double w = to_f64(val[e]) * (normalized ? dinv[r] * dinv[r] : 1.0);
+    if (Fd) {
+      for (int t = 0; t < p; ++t) M[t] += w * Fd[(size_t)r * p + t];
+    } else {
+      M[lab[r]] += w;
+    }
+  }
+  const size_t pn = (size_t)n * 4;
+  for (int t = 0; t < kpad; ++t) {
+    const double f = Fd ? (t < p ? Fd[(size_t)c * p + t] : 0.0) : (t == (int)lab[c] ? 1.0 : 0.0);
+    const double kv = normalized ? dinv[c] * (f - M[t]) : deg[c] * f - M[t];
+    const size_t at = (size_t)(t >> 2) * pn + (size_t)c * 4 + (t & 3);
+    if (K64) K64[at] = kv;
+    if (K32) K32[at] = (float)kv;
+  }
+}
+
+void launch_kmat(int n, const int32_t* row_ptr, const int32_t* col, const void* val, int val_dtype, const uint8_t* lab,
+                 const double* Fd, int p, int h, const double* dinv64, const double* deg, int normalized,
+                 double* K64, float* K32, cudaStream_t s) {
+  const int kpad = (h + 3) & ~3;
+  if (kpad > kMaxGroups) fail(SFAIRSC_ERR_UNSUPPORTED, "more than 32 constraint columns");
+  const int grid = (n + 255) / 256;
+  switch (val_dtype) {
+    case SFAIRSC_F64:
+      kmat_kernel<double><<<grid, 256, 0, s>>>(n, row_ptr, col, static_cast<const double*>(val), lab, Fd, p, kpad,
+                                                dinv64, deg, normalized, K64, K32);
+      break;
+    case SFAIRSC_F32:
+      kmat_kernel<float><<<grid, 256, 0, s>>>(n, row_ptr, col, static_cast<const float*>(val), lab, Fd, p, kpad,
+                                               dinv64, deg, normalized, K64, K32);
+      break;
+    default:
+      kmat_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(n, row_ptr, col, static_cast<const __nv_bfloat16*>(val), lab,
+                                                       Fd, p, kpad, dinv64, deg, normalized, K64, K32);
+  }
+  check_cuda(cudaGetLastError(), "kmat launch");
+}
+
 }  // namespace sfairsc
