@@ -90,15 +90,27 @@ class FairSC:
         res = O.t()
         return res.reshape(-1) if vec else res
 
-    def solve(self, want_labels: bool = True, allow_not_converged: bool = False, on_host: bool = False):
-        """Eigenvalues (k,), H (n, k) and labels (n,) plus the info dict."""
-        dev = torch.device("cpu") if on_host else self.device
-        lam = torch.empty(self.k, dtype=torch.float64, device=dev)
-        H = torch.empty(self.n, self.k, dtype=torch.float64, device=dev)
-        lab = torch.empty(self.n, dtype=torch.int32, device=dev) if want_labels else None
-        if on_host:
-            lam, H = lam.pin_memory(), H.pin_memory()
-            lab = lab.pin_memory() if lab is not None else None
+    def solve(self, want_labels: bool = True, allow_not_converged: bool = False, on_host: bool = False,
+              out: tuple | None = None):
+        """Eigenvalues (k,), H (n, k) and labels (n,) plus the info dict.  out = (lam, H, labels)
+        writes into caller-owned tensors (float64 (k,), float64 (n, k), int32 (n,) or None; host or
+        device, contiguous), e.g. pinned host buffers allocated once for repeated solves."""
+        if out is not None:
+            lam, H, lab = out
+            if lam.dtype != torch.float64 or lam.numel() != self.k or not lam.is_contiguous():
+                raise ValueError("out[0] must be a contiguous float64 tensor of k values")
+            if H.dtype != torch.float64 or H.shape != (self.n, self.k) or not H.is_contiguous():
+                raise ValueError("out[1] must be a contiguous float64 (n, k) tensor")
+            if lab is not None and (lab.dtype != torch.int32 or lab.numel() != self.n or not lab.is_contiguous()):
+                raise ValueError("out[2] must be a contiguous int32 tensor of n values")
+        else:
+            dev = torch.device("cpu") if on_host else self.device
+            lam = torch.empty(self.k, dtype=torch.float64, device=dev)
+            H = torch.empty(self.n, self.k, dtype=torch.float64, device=dev)
+            lab = torch.empty(self.n, dtype=torch.int32, device=dev) if want_labels else None
+            if on_host:
+                lam, H = lam.pin_memory(), H.pin_memory()
+                lab = lab.pin_memory() if lab is not None else None
         allow = (0, -7) if allow_not_converged else (0,)
         rc, info = B.sfairsc_solve(self.ctx, _ptr(lam), _ptr(H), _ptr(lab), allow)
         self.info = info.as_dict()

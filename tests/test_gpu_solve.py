@@ -229,3 +229,23 @@ def test_tensor_core_restart(built_lib, orth_mode):
     assert abs(i0["restarts"] - i1["restarts"]) <= 1, (i0["restarts"], i1["restarts"])
     assert i0["dorth_err"] <= 1e-6, i0["dorth_err"]
     assert eig_rel_err(l0, l1, float(i0["sigma"]), 1e-4) <= 1e-4
+
+
+def test_solve_into_caller_buffers(built_lib):
+    """solve(out=...) writes into caller-owned tensors (pinned host here, allocated once) the same
+    values as a solve into fresh device tensors."""
+    from paper_2210_16435_gb300.solver import FairSC
+
+    g = configs.msbm_n2000_k5_h2()["graph"]
+    rp, ci, v, gr = graph_tensors(g)
+    s = FairSC(rp, ci, v, gr, k=5, h=2, prec="mixed", block=4)
+    lam, H, lab, _ = s.solve()
+    outs = (torch.empty(5, dtype=torch.float64).pin_memory(), torch.empty(g.n, 5, dtype=torch.float64).pin_memory(),
+            torch.empty(g.n, dtype=torch.int32).pin_memory())
+    for _ in range(2):
+        l2, H2, lab2, _ = s.solve(out=outs)
+        assert l2 is outs[0] and H2 is outs[1] and lab2 is outs[2]
+        assert torch.equal(l2, lam.cpu()) and torch.equal(H2, H.cpu()) and torch.equal(lab2, lab.cpu())
+    with pytest.raises(ValueError):
+        s.solve(out=(outs[0], outs[1][:, :4], outs[2]))
+    s.close()
