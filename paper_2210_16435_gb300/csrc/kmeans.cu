@@ -268,13 +268,18 @@ template <int DMAX>
 __global__ void __launch_bounds__(256, 3) assign_kernel(int n, int d, int k, const float* __restrict__ X32, const double* __restrict__ mu,
                               int* lab, float* dist, unsigned* changed, const int* __restrict__ done, float one) {
   static_assert(DMAX % 2 == 0, "dimension pairs");
-  extern __shared__ float msh[];  // k x dp, dp = d rounded up to even, zero padded
+  // centroids in groups of four, interleaved by dimension pair: element (c, j) at
+  // ((c / 4) * dp / 2 + j / 2) * 8 + (c % 4) * 2 + j % 2, so one 16-byte load brings a dimension pair of
+  // two centroids (dp = d rounded up to even, zero padded; k rounded up to 4 with zero centroids)
+  extern __shared__ float msh[];
   const int r = blockIdx.y;
   if (done[r]) return;
   const int dp = (d + 1) & ~1;
-  for (int t = threadIdx.x; t < k * dp; t += blockDim.x) {
+  const int k4 = (k + 3) & ~3;
+  for (int t = threadIdx.x; t < k4 * dp; t += blockDim.x) {
     const int c = t / dp, j = t - c * dp;
-    msh[t] = j < d ? __double2float_rn(mu[(size_t)r * k * d + (size_t)c * d + j]) : 0.f;
+    msh[((c >> 2) * (dp >> 1) + (j >> 1)) * 8 + (c & 3) * 2 + (j & 1)] =
+        (c < k && j < d) ? __double2float_rn(mu[(size_t)r * k * d + (size_t)c * d + j]) : 0.f;
   }
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -298,17 +303,17 @@ __global__ void __launch_bounds__(256, 3) assign_kernel(int n, int d, int k, con
     // four centroids at a time: four independent chains of adds (each in dimension order) keep the
     // FMA pipe busy between the dependent adds of one chain
     for (int c = 0; c < k; c += 4) {
-      const float2* m[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) m[q] = reinterpret_cast<const float2*>(msh + (size_t)min(c + q, k - 1) * dp);
+      const float4* mg = reinterpret_cast<const float4*>(msh + (size_t)(c >> 2) * (dp >> 1) * 8);
       float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int j2 = 0; j2 < DMAX / 2; ++j2) {
         if (2 * j2 < d) {
           const unsigned long long xp = pack2(x[2 * j2], x[2 * j2 + 1]);
+          const float4 m01 = mg[2 * j2], m23 = mg[2 * j2 + 1];
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            const float2 p = m[q][j2];
+            const float2 p = q == 0 ? make_float2(m01.x, m01.y) : q == 1 ? make_float2(m01.z, m01.w)
+                           : q == 2 ? make_float2(m23.x, m23.y) : make_float2(m23.z, m23.w);
             const unsigned long long t = sub2_rn(xp, pack2(p.x, p.y));
             float s0, s1;
             unpack2(mul2_rn(t, t), s0, s1);
@@ -579,7 +584,7 @@ KmeansResult run_kmeans(int64_t n64, int d, const double* X, int kc, uint64_t se
       xshift = 62 - bitlen((uint64_t)n) - e;
     }
     const size_t msmem = sizeof(float) * (size_t)k * d;
-    const size_t amsmem = sizeof(float) * (size_t)k * ((d + 1) & ~1);  // padded rows for assign_kernel
+    const size_t amsmem = sizeof(float) * (size_t)((k + 3) & ~3) * ((d + 1) & ~1);  // padded for assign_kernel
     const size_t ssmem = sizeof(long long) * ((size_t)k * d + k);
     const int rows_per_warp = 64;
     const int ub = 256;
