@@ -16,7 +16,9 @@
 #include <cstdio>
 #include <cstring>
 #include <limits>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -50,6 +52,56 @@ static bool is_device_ptr(const void* p) {
 }
 
 static size_t dtype_size(int dt) { return dt == SFAIRSC_F64 ? 8 : dt == SFAIRSC_F32 ? 4 : 2; }
+
+// Device memory of the contexts comes from one stream-ordered pool per device that keeps the blocks
+// it gets back (release threshold: never), so creating and destroying contexts again and again (a
+// solve per request) re-uses memory instead of mapping and unmapping it every time.  The pool
+// holds, until the process ends, as much as the largest set of contexts alive at once needed.
+static cudaMemPool_t context_pool() {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  check_cuda(cudaGetDevice(&dev), "get device");
+  if (dev < 0 || dev >= 64) fail(SFAIRSC_ERR_UNSUPPORTED, "device index above 63");
+  std::lock_guard<std::mutex> lk(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    check_cuda(cudaMemPoolCreate(&pool, &props), "memory pool");
+    uint64_t keep = ~0ull;
+    check_cuda(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep), "memory pool threshold");
+    pools[dev] = pool;
+  }
+  return pools[dev];
+}
+
+// Pinned host staging buffers of the contexts (a few small ones each), kept by size for the next
+// context: pinning host memory costs far more than the buffers' use.
+static std::mutex g_pinned_mu;
+static std::multimap<size_t, void*> g_pinned_free;
+static void* pinned_get(size_t bytes) {
+  {
+    std::lock_guard<std::mutex> lk(g_pinned_mu);
+    auto it = g_pinned_free.find(bytes);
+    if (it != g_pinned_free.end()) {
+      void* p = it->second;
+      g_pinned_free.erase(it);
+      return p;
+    }
+  }
+  void* p = nullptr;
+  check_cuda(cudaMallocHost(&p, bytes), "pinned allocation");
+  return p;
+}
+static void pinned_put(void* p, size_t bytes) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_pinned_mu);
+  if (g_pinned_free.size() < 64) g_pinned_free.emplace(bytes, p);
+  else cudaFreeHost(p);
+}
 
 }  // namespace sfairsc
 
@@ -152,20 +204,23 @@ struct sfairsc_ctx {
   template <typename T>
   T* dalloc(size_t count) {
     void* p = nullptr;
-    check_cuda(cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T)), "device allocation");
+    check_cuda(cudaMallocFromPoolAsync(&p, std::max<size_t>(count, 1) * sizeof(T), context_pool(), stream),
+               "device allocation");
     owned.push_back(p);
     return static_cast<T*>(p);
   }
+  size_t hh_bytes = 0, yh_bytes = 0, ys_bytes = 0;
   ~sfairsc_ctx() {
     for (auto& pr : ev_op) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     for (auto& pr : ev_orth) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     for (auto& pr : ev_restart) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
-    for (void* p : owned) cudaFree(p);
-    if (Hh) cudaFreeHost(Hh);
-    if (Yh) cudaFreeHost(Yh);
-    if (Ystage) cudaFreeHost(Ystage);
-    if (params_host) cudaFreeHost(params_host);
+    for (void* p : owned) cudaFreeAsync(p, stream);  // back to the pool in stream order
+    cudaStreamSynchronize(stream);
+    pinned_put(Hh, hh_bytes);
+    pinned_put(Yh, yh_bytes);
+    pinned_put(Ystage, ys_bytes);
+    pinned_put(params_host, sizeof(double) * kParams);
   }
 };
 
@@ -193,9 +248,7 @@ int guarded(F&& f) {
 template <typename T>
 const T* to_device(sfairsc_ctx* c, const T* p, size_t count, size_t elem = sizeof(T)) {
   if (is_device_ptr(p)) return p;
-  void* d = nullptr;
-  check_cuda(cudaMalloc(&d, std::max<size_t>(count * elem, 1)), "device allocation");
-  c->owned.push_back(d);
+  void* d = c->dalloc<unsigned char>(std::max<size_t>(count * elem, 1));
   check_cuda(cudaMemcpyAsync(d, p, count * elem, cudaMemcpyHostToDevice, c->stream), "host to device copy");
   return static_cast<const T*>(d);
 }
@@ -287,7 +340,7 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
       c->z[g] = cnt[g] / (double)n;
       Ssum += S[g];
     }
-  check_cuda(cudaMallocHost((void**)&c->params_host, sizeof(double) * kParams), "pinned allocation");
+  c->params_host = static_cast<double*>(pinned_get(sizeof(double) * kParams));
   double* P = c->params_host;
   std::fill(P, P + kParams, 0.0);
   for (int g = 0; g < h; ++g) P[kPZ + g] = c->z[g];
@@ -520,9 +573,11 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   q.sweeps = c->sweeps;
   q.wait_ns = wait_ns;
   q.pend = c->dalloc<double>(256 * 4);
-  check_cuda(cudaMallocHost((void**)&c->Hh, sizeof(double) * c->ldh * m), "pinned allocation");
-  check_cuda(cudaMallocHost((void**)&c->Yh, sizeof(double) * m * m), "pinned allocation");
-  check_cuda(cudaMallocHost(&c->Ystage, sizeof(double) * m * m), "pinned allocation");
+  c->hh_bytes = sizeof(double) * c->ldh * m;
+  c->yh_bytes = c->ys_bytes = sizeof(double) * m * m;
+  c->Hh = static_cast<double*>(pinned_get(c->hh_bytes));
+  c->Yh = static_cast<double*>(pinned_get(c->yh_bytes));
+  c->Ystage = pinned_get(c->ys_bytes);
 
   // final-stage buffers
   const int k = c->k;

@@ -8,7 +8,7 @@
 // eigenvector matrix, so both are recorded and the vectors are formed
 // afterwards row by row: row r of Q is e_r^T H_0 H_1 ... G_1 G_2 ..., the
 // same operations on each row as accumulating Q transform by transform.
-// Rows are independent, so blocks of rows go to a few host threads.
+// Rows are independent, so ranges of rows go to a few host threads.
 #include <algorithm>
 #include <cmath>
 #include <limits>
@@ -66,8 +66,15 @@ bool host_symmetric_eig(int m, double* A, double* w, int max_sweeps) {
     for (int i = 0; i < len; ++i) vp += v[i] * p[i];
     const double K = 0.5 * beta * vp;
     for (int i = 0; i < len; ++i) wv[i] = p[i] - K * v[i];
-    for (int j = 0; j < len; ++j)
-      for (int i = 0; i < len; ++i) a(k + 1 + i, k + 1 + j) -= v[i] * wv[j] + wv[i] * v[j];
+    {
+      const double* __restrict__ vr = v;
+      const double* __restrict__ wr = wv.data();
+      for (int j = 0; j < len; ++j) {
+        double* __restrict__ colj = &A[(size_t)(k + 1 + j) * m + k + 1];
+        const double vj = vr[j], wj = wr[j];
+        for (int i = 0; i < len; ++i) colj[i] -= vr[i] * wj + wr[i] * vj;
+      }
+    }
     a(k + 1, k) = alpha;
     a(k, k + 1) = alpha;
     for (int i = 1; i < len; ++i) {
@@ -131,66 +138,57 @@ bool host_symmetric_eig(int m, double* A, double* w, int max_sweeps) {
     where[c] = order[c];
   }
 
-  // Rows [r0, r1) of Q = I H_0 H_1 ... (rotations in order), written to A's
-  // columns in ascending eigenvalue order.  A is free: d and e hold T.  Eight
-  // rows at a time, held column by column (x[j * 8 + t] = row t's entry j),
-  // so every reflector and rotation acts on contiguous 8-row vectors.
+  // Rows [r0, r1) of Q = I H_0 H_1 ... (rotations in order), written to A's columns in ascending
+  // eigenvalue order (A is free: d and e hold T).  A thread's rows are held column by column
+  // (x[j * W + t] = row r0 + t's entry j), so every reflector and rotation acts on a contiguous run
+  // of W values and each thread reads the recorded transforms once.
   auto rows = [&](int r0, int r1) {
-    constexpr int W = 8;
-    std::vector<double> x((size_t)m * W);
-    for (int b0 = r0; b0 < r1; b0 += W) {
-      const int nr = std::min(W, r1 - b0);
-      std::fill(x.begin(), x.end(), 0.0);
-      for (int t = 0; t < nr; ++t) x[(size_t)(b0 + t) * W + t] = 1.0;
-      for (int k = 0; k + 2 < m; ++k) {
-        const double beta = rbeta[k];
-        if (beta == 0.0) continue;
-        const double* v = &refl[(size_t)k * m + k + 1];
-        const int len = m - k - 1;
-        double s[W] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int j = 0; j < len; ++j) {
-          const double* xj = &x[(size_t)(k + 1 + j) * W];
-          for (int t = 0; t < W; ++t) s[t] += xj[t] * v[j];
-        }
-        for (int t = 0; t < W; ++t) s[t] *= beta;
-        for (int j = 0; j < len; ++j) {
-          double* xj = &x[(size_t)(k + 1 + j) * W];
-          for (int t = 0; t < W; ++t) xj[t] -= s[t] * v[j];
-        }
+    const int W = r1 - r0;
+    if (W <= 0) return;
+    std::vector<double> x((size_t)m * W, 0.0), sbuf(W);
+    for (int t = 0; t < W; ++t) x[(size_t)(r0 + t) * W + t] = 1.0;
+    for (int k = 0; k + 2 < m; ++k) {
+      const double beta = rbeta[k];
+      if (beta == 0.0) continue;
+      const double* v = &refl[(size_t)k * m + k + 1];
+      const int len = m - k - 1;
+      double* s = sbuf.data();
+      for (int t = 0; t < W; ++t) s[t] = 0.0;
+      for (int jj = 0; jj < len; ++jj) {
+        const double* xj = &x[(size_t)(k + 1 + jj) * W];
+        const double vj = v[jj];
+        for (int t = 0; t < W; ++t) s[t] += xj[t] * vj;
       }
-      for (const Rotation& g : rot) {
-        double* x0 = &x[(size_t)g.k * W];
-        double* x1 = x0 + W;
-        for (int t = 0; t < W; ++t) {
-          const double a0 = x0[t], a1 = x1[t];
-          x0[t] = g.c * a0 - g.s * a1;
-          x1[t] = g.s * a0 + g.c * a1;
-        }
+      for (int t = 0; t < W; ++t) s[t] *= beta;
+      for (int jj = 0; jj < len; ++jj) {
+        double* xj = &x[(size_t)(k + 1 + jj) * W];
+        const double vj = v[jj];
+        for (int t = 0; t < W; ++t) xj[t] -= s[t] * vj;
       }
-      for (int c = 0; c < m; ++c)
-        for (int t = 0; t < nr; ++t) A[(size_t)c * m + b0 + t] = x[(size_t)where[c] * W + t];
     }
+    for (const Rotation& g : rot) {
+      double* x0 = &x[(size_t)g.k * W];
+      double* x1 = x0 + W;
+      const double c = g.c, sn = g.s;
+      for (int t = 0; t < W; ++t) {
+        const double a0 = x0[t], a1 = x1[t];
+        x0[t] = c * a0 - sn * a1;
+        x1[t] = sn * a0 + c * a1;
+      }
+    }
+    for (int c = 0; c < m; ++c)
+      for (int t = 0; t < W; ++t) A[(size_t)c * m + r0 + t] = x[(size_t)where[c] * W + t];
   };
-  // whole 8-row blocks per thread
-  const int nb = (m + 7) / 8;
+  // one contiguous row range per thread, a few threads (more add start-up cost than they save at
+  // m ~ 100)
   const unsigned hw = std::thread::hardware_concurrency();
-  const int nt = m < 48 ? 1 : (int)std::min<unsigned>({8u, std::max(1u, hw / 2), (unsigned)nb});
+  const int nt = m < 48 ? 1 : (int)std::min<unsigned>({4u, std::max(1u, hw / 2), (unsigned)((m + 7) / 8)});
   if (nt <= 1) {
     rows(0, m);
   } else {
-    auto range = [&](int t, int& lo, int& hi2) {
-      lo = std::min(m, (t * nb / nt) * 8);
-      hi2 = std::min(m, ((t + 1) * nb / nt) * 8);
-    };
     std::vector<std::thread> pool;
-    for (int t = 1; t < nt; ++t) {
-      int lo, hi2;
-      range(t, lo, hi2);
-      pool.emplace_back(rows, lo, hi2);
-    }
-    int lo, hi2;
-    range(0, lo, hi2);
-    rows(lo, hi2);
+    for (int t = 1; t < nt; ++t) pool.emplace_back(rows, t * m / nt, (t + 1) * m / nt);
+    rows(0, m / nt);
     for (auto& th : pool) th.join();
   }
   return hi <= 0;
