@@ -70,6 +70,17 @@ __device__ __forceinline__ int scale_shift(float maxv, long long n) {
 // as fma(., +-one, .) with one = 1 from the launch (exact like a plain add, on the FMA pipe)
 __device__ __forceinline__ float dist_rn(const float* x, const float* m, int d, float one) {
   float acc = 0.f;
+  if ((d & 1) == 0) {  // rows of even length start 8-byte aligned: the point's coordinates two at a time
+    const float2* x2 = reinterpret_cast<const float2*>(x);
+    for (int j2 = 0; j2 < (d >> 1); ++j2) {
+      const float2 xv = x2[j2];
+      const float t0 = __fmaf_rn(m[2 * j2], -one, xv.x);
+      acc = __fmaf_rn(acc, one, __fmul_rn(t0, t0));
+      const float t1 = __fmaf_rn(m[2 * j2 + 1], -one, xv.y);
+      acc = __fmaf_rn(acc, one, __fmul_rn(t1, t1));
+    }
+    return acc;
+  }
   for (int j = 0; j < d; ++j) {
     const float t = __fmaf_rn(m[j], -one, x[j]);
     acc = __fmaf_rn(acc, one, __fmul_rn(t, t));

@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
   double* red = reinterpret_cast<double*>(smraw);                                     // kOW x kRed, between sweeps
   VT* cfs = reinterpret_cast<VT*>(smraw + (size_t)kOW * kWarpBuf);                    // coefficients c*B + v
   double* scratch = reinterpret_cast<double*>(smraw + (size_t)kOW * kWarpBuf + sizeof(VT) * kCoefMax);
-  __shared__ double gram_s[16], R1[16], R2[16], Rd1[16], Rd2[16], unorm[4];
+  __shared__ double gram_s[16], R1[16], R2[16], Rd1[16], Rd2[16], unorm[4], Rdi1[4], Rdi2[4];
   __shared__ int brk, again;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int r0 = a.cta_rows[blockIdx.x], r1 = a.cta_rows[blockIdx.x + 1];
@@ -759,6 +759,9 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
     for (int q = 0; q < B; ++q)
 #pragma unroll
       for (int v = 0; v < B; ++v) rd[q][v] = (VT)Rd1[q * B + v];
+    VT rdi[B];  // reciprocals of the diagonal: one division per thread, multiplications per row
+#pragma unroll
+    for (int v = 0; v < B; ++v) rdi[v] = VT(1) / rd[v][v];
     auto rows = [&](int lo, int hi) {
       int nb = 0;
       for (int rb = lo + threadIdx.x; rb < hi; rb += 4 * kOT) {
@@ -776,7 +779,7 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
               VT s = u[t][v];
 #pragma unroll
               for (int q = 0; q < v; ++q) s -= u[t][q] * rd[q][v];
-              u[t][v] = s / rd[v][v];
+              u[t][v] = s * rdi[v];
             }
             if (rb + t * kOT < hi) st4(U + (size_t)(rb + t * kOT) * 4, u[t]);
           }
@@ -816,7 +819,7 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
   // Cholesky of gram_s = R^T R (R upper).  A column whose remaining norm
   // vanishes relative to its input norm marks a breakdown: its row of R is
   // zero (as recorded in H) and Rd keeps a unit divisor.
-  auto cholesky = [&](double* R, double* Rd) {
+  auto cholesky = [&](double* R, double* Rd, double* Rdi) {
     if (threadIdx.x == 0) {
       for (int i = 0; i < B * B; ++i) R[i] = Rd[i] = 0.0;
       for (int c = 0; c < B; ++c) {
@@ -841,6 +844,8 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
         }
       }
     }
+    if (threadIdx.x == 0)
+      for (int v = 0; v < B; ++v) Rdi[v] = 1.0 / Rd[v * B + v];
     __syncthreads();
   };
 
@@ -945,10 +950,10 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
     if (!grid_sync(a.bar, a.err, a.wait_ns)) return;
     reduce_all(a.partial, kStride, gridDim.x, kGramOff, B * B, gram_s, scratch);
   }
-  cholesky(R1, Rd1);
+  cholesky(R1, Rd1, Rdi1);
 
   // deferred mode: e1 = c2 R1^{-1} (J x B) in scratch, the pending correction after the first QR
-  auto pending_times_rinv = [&](const double* Rd, bool from_coef) {
+  auto pending_times_rinv = [&](const double* Rd, const double* Rdi, bool from_coef) {
     if ((int)threadIdx.x < J) {
       const int c = threadIdx.x;
       double x[4];
@@ -960,14 +965,14 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
         double t = x[v];
 #pragma unroll
         for (int q = 0; q < v; ++q) t -= x[q] * Rd[q * B + v];
-        x[v] = t / Rd[v * B + v];
+        x[v] = t * Rdi[v];
       }
 #pragma unroll
       for (int v = 0; v < B; ++v) scratch[c * B + v] = x[v];
     }
     __syncthreads();
   };
-  if (defer) pending_times_rinv(Rd1, true);
+  if (defer) pending_times_rinv(Rd1, Rdi1, true);
   if (B > 1) {
     // Cholesky QR a second time: U <- U R1^{-1}, Gram again
     double e1tv = 0.0;  // thread v * B + w: (e1^T e1)_vw
@@ -990,8 +995,8 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
     }
     if (threadIdx.x < B) unorm[threadIdx.x] = 0.0;
     __syncthreads();
-    cholesky(R2, Rd2);
-    if (defer) pending_times_rinv(Rd2, false);
+    cholesky(R2, Rd2, Rdi2);
+    if (defer) pending_times_rinv(Rd2, Rdi2, false);
   } else {
     if (threadIdx.x == 0) {
       R2[0] = 1.0;
@@ -1007,6 +1012,9 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
   for (int q = 0; q < B; ++q)
 #pragma unroll
     for (int v = 0; v < B; ++v) rf[q][v] = (VT)(B > 1 ? Rd2[q * B + v] : Rd1[q * B + v]);
+  VT rfi[B];
+#pragma unroll
+  for (int v = 0; v < B; ++v) rfi[v] = VT(1) / rf[v][v];
   auto final_rows = [&](int lo, int hi) {
     for (int rb = lo + threadIdx.x; rb < hi; rb += 4 * kOT) {
       VT u[4][4];
@@ -1022,7 +1030,7 @@ __global__ void __launch_bounds__(kOT, 1) orth_kernel(OrthArgs<VT> a) {
           VT s = u[t][v];
 #pragma unroll
           for (int q = 0; q < v; ++q) s -= u[t][q] * rf[q][v];
-          u[t][v] = s / rf[v][v];
+          u[t][v] = s * rfi[v];
         }
         if (B == 4) {  // then J % 4 == 0: the block fills panel J / 4
           st4(Vp + (size_t)r * 4, u[t]);
