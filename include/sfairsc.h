@@ -67,7 +67,7 @@ typedef enum {
   SFAIRSC_ERR_CUDA = -9,            /* a CUDA runtime call failed */
   SFAIRSC_ERR_OOM = -10,            /* device or pinned-host allocation failed */
   SFAIRSC_ERR_DEVICE_TIMEOUT = -11, /* a bounded device-side wait gave up (the kernel returned early) */
-  SFAIRSC_ERR_UNSUPPORTED = -12,    /* a valid request outside this build's limits (h > 32, no sm_103a device) */
+  SFAIRSC_ERR_UNSUPPORTED = -12,    /* a valid request outside the library's limits (h > 32, no sm_103a device) */
   SFAIRSC_ERR_BREAKDOWN = -13       /* the Krylov block lost rank (exactly invariant subspace) */
 } sfairsc_status;
 

@@ -124,8 +124,8 @@ def paper_msbm(n: int, h: int, k: int = 5, seed: int = 0):
 
 def random_laplacian(n: int, h: int = 5, k: int = 5, mean_degree: float = 100.0, seed: int = 0):
     """The random-Laplacian workload of Exp. 4: a random sparse symmetric W and a random dense F
-    (the paper does not state the sparsity of this experiment; mean degree 100 is this build's
-    reading)."""
+    (the paper does not state the sparsity of this experiment; mean degree 100 is the reading
+    taken here)."""
     g = random_weighted_graph(n, min(1.0, mean_degree / (n - 1)), seed=seed * 1000 + 11)
     F = random_constraints(n, h - 1, seed=seed * 1000 + 12)
     return {"name": f"random_laplacian_n{n}_h{h}", "graph": g, "F": F, "k": k, "h": h, "value_dtype": "f64",

@@ -210,11 +210,16 @@ struct sfairsc_ctx {
     return static_cast<T*>(p);
   }
   size_t hh_bytes = 0, yh_bytes = 0, ys_bytes = 0;
+  cudaStream_t side = nullptr;  // host copies that overlap device work
   ~sfairsc_ctx() {
     for (auto& pr : ev_op) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     for (auto& pr : ev_orth) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     for (auto& pr : ev_restart) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    if (side) {
+      cudaStreamSynchronize(side);
+      cudaStreamDestroy(side);
+    }
     for (void* p : owned) cudaFreeAsync(p, stream);  // back to the pool in stream order
     cudaStreamSynchronize(stream);
     pinned_put(Hh, hh_bytes);
@@ -1020,9 +1025,21 @@ int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* label
     else
       std::memcpy(eigenvalues, c->lam_h.data(), sizeof(double) * k);
   }
-  if (Hout)
+  // H to host memory on a side stream, so the copy runs under the k-means (which only reads H)
+  cudaEvent_t h_copied = nullptr;
+  if (Hout && !is_device_ptr(Hout) && labels) {
+    if (!c->side) check_cuda(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "side stream");
+    cudaEvent_t h_ready = c->take_event();
+    h_copied = c->take_event();
+    check_cuda(cudaEventRecord(h_ready, s), "event record");
+    check_cuda(cudaStreamWaitEvent(c->side, h_ready, 0), "stream wait");
+    check_cuda(cudaMemcpyAsync(Hout, c->Hres, sizeof(double) * n * k, cudaMemcpyDeviceToHost, c->side), "copy H");
+    check_cuda(cudaEventRecord(h_copied, c->side), "event record");
+    c->ev_pool.push_back(h_ready);  // reusable once recorded work completes (the stream is synchronised below)
+  } else if (Hout) {
     check_cuda(cudaMemcpyAsync(Hout, c->Hres, sizeof(double) * n * k,
                                is_device_ptr(Hout) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s), "copy H");
+  }
   if (labels) {
     Timer tk(s);
     const KmeansResult kr = run_kmeans(n, k, c->Hres, k, c->opts.kmeans_seed, c->opts.kmeans_n_init,
@@ -1033,6 +1050,10 @@ int solve_impl(sfairsc_ctx* c, double* eigenvalues, double* Hout, int32_t* label
     check_cuda(cudaMemcpyAsync(labels, c->labels_d, sizeof(int32_t) * n,
                                is_device_ptr(labels) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s), "copy labels");
     inf.ms_kmeans = tk.stop(s);
+  }
+  if (h_copied) {
+    check_cuda(cudaStreamWaitEvent(s, h_copied, 0), "stream wait");
+    c->ev_pool.push_back(h_copied);
   }
   check_cuda(cudaStreamSynchronize(s), "solve end");
   c->solved = true;

@@ -351,15 +351,27 @@ __global__ void colargmax_kernel(int n, int k, const double* __restrict__ X, uns
   }
 }
 
-__global__ void embed_kernel(int n, int k, const double* __restrict__ X, const double* __restrict__ dinv,
-                             int normalized, const unsigned long long* colkey, double* H) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n) return;
-  const double sc = normalized ? dinv[r] : 1.0;
-  for (int c = 0; c < k; ++c) {
-    const double piv = X[(size_t)c * n + colkey[k + c]];
-    const double sg = piv < 0.0 ? -1.0 : 1.0;
-    H[(size_t)r * k + c] = sg * sc * X[(size_t)c * n + r];
+// H = sign_c D^{-1/2} X through a shared tile of 32 rows: X is read a column at a time (32
+// consecutive doubles per column) and H written a row block at a time (32 k consecutive doubles),
+// both coalesced.
+constexpr int kEmbRows = 32;
+__global__ void __launch_bounds__(256) embed_kernel(int n, int k, const double* __restrict__ X,
+                                                    const double* __restrict__ dinv, int normalized,
+                                                    const unsigned long long* colkey, double* H) {
+  extern __shared__ double tile[];  // kEmbRows x (k + 1), plus k signs
+  double* sg = tile + kEmbRows * (k + 1);
+  const int r0 = blockIdx.x * kEmbRows;
+  const int rows = min(kEmbRows, n - r0);
+  for (int c = threadIdx.x; c < k; c += blockDim.x) sg[c] = X[(size_t)c * n + colkey[k + c]] < 0.0 ? -1.0 : 1.0;
+  for (int e = threadIdx.x; e < kEmbRows * k; e += blockDim.x) {
+    const int c = e / kEmbRows, rr = e % kEmbRows;
+    if (rr < rows) tile[rr * (k + 1) + c] = X[(size_t)c * n + r0 + rr];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < rows * k; e += blockDim.x) {
+    const int rr = e / k, c = e % k;
+    const double sc = normalized ? dinv[r0 + rr] : 1.0;
+    H[(size_t)(r0 + rr) * k + c] = sg[c] * sc * tile[rr * (k + 1) + c];
   }
 }
 
@@ -377,7 +389,10 @@ void launch_embed(int n, int k, const double* X, const double* dinv64, int norma
   dim3 g(min(152 * 2, (n + 255) / 256), k);
   colmax_kernel<<<g, 256, 0, s>>>(n, k, X, colkey);
   colargmax_kernel<<<g, 256, 0, s>>>(n, k, X, colkey);
-  embed_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, k, X, dinv64, normalized, colkey, H);
+  const size_t smem = sizeof(double) * ((size_t)kEmbRows * (k + 1) + k);
+  if (smem > 48 * 1024)
+    check_cuda(cudaFuncSetAttribute(embed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), "embed smem");
+  embed_kernel<<<(n + kEmbRows - 1) / kEmbRows, 256, smem, s>>>(n, k, X, dinv64, normalized, colkey, H);
   check_cuda(cudaGetLastError(), "embed launch");
 }
 
