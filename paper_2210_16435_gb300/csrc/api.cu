@@ -141,7 +141,7 @@ struct sfairsc_ctx {
   OpPlan proj64;  // FP64 projection P w only
   void* ytil = nullptr;
   double* ytil64 = nullptr;
-  double* dfT = nullptr;  // n x 4 FP64: L_n X of the final check (MIXED)
+  double* dfT = nullptr;  // n x 8 FP64: L_n X of the final check (MIXED)
   double* op_partial = nullptr;
   int32_t* cta_rows = nullptr;
   int32_t* cta_rows_orth = nullptr;
@@ -427,8 +427,9 @@ void build_context(sfairsc_ctx* c, const int32_t* row_ptr, const int32_t* col_id
   const int batch_rows = (int)std::max(1ll, std::min(32ll, (long long)n / grid / 64));
   const size_t vs = c->vt == VecType::F64 ? 8 : 4;
   c->ytil = c->dalloc<unsigned char>((size_t)n * 4 * vs);
-  c->ytil64 = c->dalloc<double>((size_t)n * 4);
-  c->dfT = c->vt == VecType::F32 ? c->dalloc<double>((size_t)n * 4) : nullptr;
+  // FP64 ytil (n x 4); for the MIXED final check also the double-float ytil of 8 vectors (n x 8 pairs)
+  c->ytil64 = c->dalloc<double>((size_t)n * (c->vt == VecType::F32 ? 8 : 4));
+  c->dfT = c->vt == VecType::F32 ? c->dalloc<double>((size_t)n * 8) : nullptr;
   c->op_partial = c->dalloc<double>((size_t)grid * kMaxGroups * 4);
   // words: [0..1] the operator's 64-bit barrier counter, [2] error word,
   // [4..7] operator work counters, [8..9] the Gram-Schmidt kernel's counter
@@ -721,12 +722,17 @@ double final_check(sfairsc_ctx* c, int mv, const std::vector<double>& T, std::ve
   if (c->vt == VecType::F32) {
     // X lies in null(C^T) (projected just above), so A X = P (L_n X): the SpMV in double-float on
     // the FP32 pipe (FP64-grade), then the FP64 projection
-    for (int i = 0; i < k; i += 4) {
-      const int nv = std::min(4, k - i);
+    // eight vectors per SpMV (one pass over the edges and one gather per entry for eight columns),
+    // the FP64 projection four at a time
+    for (int i = 0; i < k;) {
+      const int nv = k - i >= 8 ? 8 : std::min(4, k - i);
       launch_df_spmv(n, c->row_ptr, c->col, c->val_orig, c->vdt_orig, c->dinv64, c->deg, c->normalized,
                      c->op64.lanes_per_row, c->X64 + (size_t)i * n, nv, c->ytil64, c->dfT, c->sms, s);
-      launch_operator(c->proj64, VecType::F64, c->dfT, 1, n, c->AX64 + (size_t)i * n, 1, n, nv, s);
+      for (int q = 0; q < nv; q += 4)
+        launch_operator(c->proj64, VecType::F64, c->dfT + (size_t)q * n, 1, n, c->AX64 + (size_t)(i + q) * n, 1, n,
+                        std::min(4, nv - q), s);
       c->n_launches += 2 + (nv + 3) / 4;
+      i += nv;
     }
   } else {
     for (int i = 0; i < k; i += 4) {

@@ -104,8 +104,8 @@ WindowTable build_window_table(int n, const int32_t* row_ptr, const int32_t* col
 // and of out is out[r*ors + v*ocs].
 void launch_operator(const OpPlan& p, VecType vt, const void* w, int64_t wrs, int64_t wcs, void* out, int64_t ors,
                      int64_t ocs, int nvec, cudaStream_t s);
-// T = L_n X (or L X unnormalized) for b <= 4 FP64 columns (column-major, ld n) with FP64-grade
-// accuracy on the FP32 pipe (double-float); ytil_pairs: workspace of n * b float pairs.
+// T = L_n X (or L X unnormalized) for b <= 4 or b = 8 FP64 columns (column-major, ld n) with
+// FP64-grade accuracy on the FP32 pipe (double-float); ytil_pairs: workspace of n * b float pairs.
 void launch_df_spmv(int n, const int32_t* row_ptr, const int32_t* col, const void* val, int val_dtype,
                     const double* dinv64, const double* deg, int normalized, int lanes, const double* X, int b,
                     void* ytil_pairs, double* T, int sms, cudaStream_t s);

@@ -359,7 +359,10 @@ __global__ void update_sums_kernel(int n, int d, int k, const float* __restrict_
   for (int i = threadIdx.x; i < k * d + k; i += blockDim.x) ssum[i] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const long long w0 = ((long long)blockIdx.x * nw + warp) * rows_per_warp;
+  // CTAs take the row blocks from the last one down: the assignment just before read the points in
+  // ascending order, so the first CTAs to run find their rows still in L2 (and the next assignment,
+  // ascending again, starts on the rows read here last)
+  const long long w0 = ((long long)(gridDim.x - 1 - blockIdx.x) * nw + warp) * rows_per_warp;
   const int* lb = lab + (size_t)r * n;
   // trunc(x 2^xshift): scaling by a power of two is exact (the scaled value
   // stays below 2^63, and one below 2^-126 truncates to 0 either way), and the

@@ -1035,13 +1035,13 @@ __global__ void __launch_bounds__(256) df_spmv_kernel(int n, const int32_t* __re
         if (c[u] >= 0) {
           F2 y[B];
           const F2* p = ytil + (size_t)c[u] * B;
-          if constexpr (B == 4) {
-            const float4 a = __ldg(reinterpret_cast<const float4*>(p));
-            const float4 bb = __ldg(reinterpret_cast<const float4*>(p) + 1);
-            y[0] = F2{a.x, a.y};
-            y[1] = F2{a.z, a.w};
-            y[2] = F2{bb.x, bb.y};
-            y[3] = F2{bb.z, bb.w};
+          if constexpr (B % 2 == 0) {  // rows of B pairs, 16-byte aligned: two pairs per load
+#pragma unroll
+            for (int q = 0; q < B / 2; ++q) {
+              const float4 a = __ldg(reinterpret_cast<const float4*>(p) + q);
+              y[2 * q] = F2{a.x, a.y};
+              y[2 * q + 1] = F2{a.z, a.w};
+            }
           } else {
 #pragma unroll
             for (int v = 0; v < B; ++v) y[v] = p[v];
@@ -1060,29 +1060,23 @@ __global__ void __launch_bounds__(256) df_spmv_kernel(int n, const int32_t* __re
         other.lo = __shfl_xor_sync(0xffffffffu, acc[v].lo, o);
         acc[v] = df_add(fa, acc[v], other);
       }
-    // every lane of the row holds its sums: lane v of the row forms column v (FP64 is a narrow pipe
-    // on this part, so the row's B FP64 results take one instruction slot, not B)
-    if (Lr >= B) {
-      if (live && sub < B) {
+    // every lane of the row holds its sums: lane sub of the row forms the columns sub, sub + Lr, ...
+    // Each column's pair is picked by FP32 selects first, so a lane issues one FP64 epilogue per
+    // column it owns: FP64 is a narrow pipe on this part, and FP64 instructions predicated off
+    // still take their issue slots (one predicated epilogue per column and lane cost 2 ms a solve).
+    if (live)
+      for (int c0 = sub; c0 < B; c0 += Lr) {
         float hi = acc[0].hi, lo = acc[0].lo;
 #pragma unroll
         for (int v = 1; v < B; ++v)
-          if (sub == v) {
+          if (c0 == v) {
             hi = acc[v].hi;
             lo = acc[v].lo;
           }
         const double s = (double)hi + (double)lo;
-        const double x = X[(size_t)r + (size_t)sub * n];
-        T[(size_t)r + (size_t)sub * n] = normalized ? x - dinv[r] * s : deg[r] * x - s;
+        const double x = X[(size_t)r + (size_t)c0 * n];
+        T[(size_t)r + (size_t)c0 * n] = normalized ? x - dinv[r] * s : deg[r] * x - s;
       }
-    } else if (live && sub == 0) {
-#pragma unroll
-      for (int v = 0; v < B; ++v) {
-        const double s = (double)acc[v].hi + (double)acc[v].lo;
-        const double x = X[(size_t)r + (size_t)v * n];
-        T[(size_t)r + (size_t)v * n] = normalized ? x - dinv[r] * s : deg[r] * x - s;
-      }
-    }
   }
 }
 
@@ -1094,6 +1088,7 @@ void df_spmv_launch(int n, const int32_t* row_ptr, const int32_t* col, const voi
   const MT* v = static_cast<const MT*>(val);
   const int grid = 8 * sms;
   switch (b) {
+    case 8: df_spmv_kernel<MT, 8><<<grid, 256, 0, s>>>(n, row_ptr, col, v, dinv, deg, normalized, Lr, X, ytil, T, 1.f); break;
     case 4: df_spmv_kernel<MT, 4><<<grid, 256, 0, s>>>(n, row_ptr, col, v, dinv, deg, normalized, Lr, X, ytil, T, 1.f); break;
     case 3: df_spmv_kernel<MT, 3><<<grid, 256, 0, s>>>(n, row_ptr, col, v, dinv, deg, normalized, Lr, X, ytil, T, 1.f); break;
     case 2: df_spmv_kernel<MT, 2><<<grid, 256, 0, s>>>(n, row_ptr, col, v, dinv, deg, normalized, Lr, X, ytil, T, 1.f); break;
@@ -1106,7 +1101,7 @@ void df_spmv_launch(int n, const int32_t* row_ptr, const int32_t* col, const voi
 void launch_df_spmv(int n, const int32_t* row_ptr, const int32_t* col, const void* val, int val_dtype,
                     const double* dinv64, const double* deg, int normalized, int lanes, const double* X, int b,
                     void* ytil_pairs, double* T, int sms, cudaStream_t s) {
-  if (b < 1 || b > 4) fail(SFAIRSC_ERR_INVALID_ARG, "df spmv block");
+  if (b < 1 || (b > 4 && b != 8)) fail(SFAIRSC_ERR_INVALID_ARG, "df spmv block");
   F2* yt = static_cast<F2*>(ytil_pairs);
   switch (val_dtype) {
     case SFAIRSC_F64:
