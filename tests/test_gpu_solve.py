@@ -149,6 +149,35 @@ def test_unnormalized_extension(built_lib):
     solve_and_check(g, 3, "fp64", normalized=False)
 
 
+def sparse_fair_clusters(k=10, per=200, h=2, matchings=4, seed=0):
+    """k clusters of `per` vertices, each the union of `matchings` random matchings (average degree
+    about 2 matchings, an expander: a wide gap above the k smallest eigenvalues), groups alternating
+    inside every cluster (each cluster is fair), consecutive clusters joined by one weak edge."""
+    from msbm import graph_from_dense
+
+    rng = np.random.default_rng(seed)
+    n = k * per
+    W = np.zeros((n, n))
+    for c in range(k):
+        base = c * per
+        for _ in range(matchings):
+            p = rng.permutation(per)
+            for i in range(per):
+                if p[i] != i:
+                    W[base + i, base + p[i]] = W[base + p[i], base + i] = 1.0
+        nb = ((c + 1) % k) * per
+        W[base, nb] = W[nb, base] = 0.05
+    return graph_from_dense(W, np.tile(np.arange(h), n // h), np.repeat(np.arange(k), per), k)
+
+
+def test_low_degree_final_check_lanes(built_lib):
+    """MIXED, k = 10, average degree below 8: the final check's double-float SpMV runs one launch
+    of eight vectors and one of two with two lanes per row, so each lane forms several columns."""
+    g = sparse_fair_clusters()
+    assert len(g.col_idx) / g.n <= 8.0  # FP64 operator lanes per row: 2
+    solve_and_check(g, 10, "mixed", block=4)
+
+
 def test_fair_cliques_exact_recovery(built_lib):
     """Disjoint exactly-fair cliques joined weakly: k-means recovers them (Err = 0)."""
     k, h, per = 4, 2, 50
