@@ -71,6 +71,13 @@ def test_lloyd_matches_sklearn_from_same_init():
                     max_iter=300).fit(X32.astype(np.float64))
     assert np.array_equal(labels, ref.labels_)
     np.testing.assert_allclose(mu, ref.cluster_centers_, rtol=1e-6, atol=1e-6)
+    # the inertia: the same sum of squared distances as scikit-learn's, and as an FP64 sum over the
+    # FP32 points (the oracle's exact fixed-point total of FP32 distances is within FP32 rounding)
+    val = km.inertia(X32, labels, mu)
+    X64 = X32.astype(np.float64)
+    direct = float(((X64 - mu[labels]) ** 2).sum())
+    assert val == pytest.approx(direct, rel=1e-5)
+    assert val == pytest.approx(ref.inertia_, rel=1e-5)
 
 
 def test_lloyd_fixed_point():

@@ -65,3 +65,19 @@ def test_balance_upper_bound_reached_by_fair_clustering():
     for _ in range(20):
         lab = rng.integers(0, 3, 100)
         assert metrics.balance(lab, groups, 3, 2).min() <= 40 / 60 + 1e-12
+
+
+def test_balance_multiset_by_hand():
+    """The sorted rows of the cluster x group count matrix: worked out by hand, unchanged by a
+    relabelling of the clusters, changed by moving one vertex, and giving eq. bal's balances."""
+    labels = np.array([0, 0, 1, 1, 1, 2])
+    groups = np.array([0, 1, 0, 0, 1, 1])
+    ms = metrics.balance_multiset(labels, groups, 3, 2)
+    assert ms == [(0, 1), (1, 1), (2, 1)]  # cluster 2: (0, 1); cluster 0: (1, 1); cluster 1: (2, 1)
+    perm = np.array([2, 0, 1])
+    assert metrics.balance_multiset(perm[labels], groups, 3, 2) == ms
+    moved = labels.copy()
+    moved[2] = 2  # a group-0 vertex from cluster 1 to cluster 2
+    assert metrics.balance_multiset(moved, groups, 3, 2) == [(1, 1), (1, 1), (1, 1)]
+    bal = sorted(min(r) / max(r) if min(r) > 0 else 0.0 for r in ms)
+    np.testing.assert_allclose(sorted(metrics.balance(labels, groups, 3, 2)), bal)
