@@ -653,6 +653,26 @@ def paper_msbm_bench(dev, sizes=(1000, 2000, 4000, 10000), fairsc_max_n=2000):
     return {"workload": "m-SBM k = 5, h in {2, 5, 10}, (a, b, c, d) = (10, 7, 4, 1) (log n / n)^(2/3)", "rows": rows}
 
 
+def step_breakdown(FairSC, inputs, outs, kw):
+    """Wall-clock milliseconds of create, solve and close for one step (synchronised between the
+    calls), with the solve's own CUDA-event times of the eigensolve and the k-means."""
+    import torch
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s = FairSC(*inputs, **kw)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    _, _, _, info = s.solve(out=outs) if outs is not None else s.solve()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    s.close()
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    return {"create_ms": (t1 - t0) * 1e3, "solve_call_ms": (t2 - t1) * 1e3, "close_ms": (t3 - t2) * 1e3,
+            "solve_events_ms": info["ms_solve"], "kmeans_events_ms": info["ms_kmeans"]}
+
+
 def cpu_baseline(args, c, FairSC, rp, ci, v, gr, kw):
     """The oracle on the host cores at the bench workload: setup + its own Lanczos to
     1e-6 sigma (complete, timed, all threads) + embedding + k-means (seeding and three
@@ -880,6 +900,14 @@ def run_ours(args):
         h2d = 4 * (g.n + 1) + 4 * g.nnz + VDT_BYTES[c["value_dtype"]] * g.nnz + 4 * g.n
         d2h = 8 * k + 8 * g.n * k + 4 * g.n
         line["e2e"] = {"value": e2e, "unit": "s/solve", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        # untimed: one step on each path split into its calls, the device synchronised between them
+        # (where the end-to-end time above the device-resident value goes)
+        try:
+            kw_e2e = dict(k=k, h=h, prec=args.prec, block=args.block)
+            line["e2e_breakdown"] = {"device_inputs": step_breakdown(FairSC, (rp, ci, v, gr), None, kw_e2e),
+                                     "host_inputs": step_breakdown(FairSC, hp, outs, kw_e2e)}
+        except Exception as ex:  # a diagnostic: it never costs the bench line
+            line["e2e_breakdown"] = {"error": repr(ex)}
         # batched form (256 graphs, one launch) against sequential single-graph solves
         if not args.no_batched:
             line["batched"] = batched_extra(dev, peak)
