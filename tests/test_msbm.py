@@ -1,6 +1,7 @@
 """The m-SBM generator (Appendix B.2): layout, structure, determinism, edge rates."""
 import numpy as np
 import pytest
+import scipy.sparse as sp
 
 from conftest import golden
 from msbm import cell_sizes_equal, cell_sizes_from_proportions, category_probabilities, sample_msbm, configs
@@ -89,3 +90,65 @@ def test_small_workload_shapes():
     assert g.n == 2000 and abs(g.nnz / g.n - 379.6) < 5
     assert np.all(np.bincount(g.groups) == 1000)
     assert np.all(np.bincount(g.clusters) == 400)
+
+
+@pytest.mark.parametrize("s", [2, 3, 5, 17, 64, 301])
+def test_tri_unrank_is_the_row_order_enumeration(s):
+    """Every rank maps to its pair (r, c), r < c, in row order: exactly np.triu_indices(s, 1)."""
+    from msbm.generator import _tri_unrank
+
+    idx = np.arange(s * (s - 1) // 2)
+    r, c = _tri_unrank(idx, np.full(idx.size, s))
+    rr, cc = np.triu_indices(s, 1)
+    assert np.array_equal(r, rr) and np.array_equal(c, cc)
+
+
+def test_tri_unrank_row_boundaries_at_large_sizes():
+    """Around every tested row start of a large cell (where a float square root alone would land in
+    the neighbouring row), the rank maps to the closed-form pair."""
+    from msbm.generator import _tri_unrank
+
+    rng = np.random.default_rng(0)
+    for s in (10**5, 999_983, 2_000_000):
+        rows = np.concatenate([[0, 1, s - 3, s - 2], rng.integers(0, s - 1, 200)])
+        start = rows * (2 * s - rows - 1) // 2
+        for off in (-1, 0, 1):
+            idx = start + off
+            ok = (idx >= 0) & (idx < s * (s - 1) // 2)
+            idx, base = idx[ok], rows[ok]
+            r, c = _tri_unrank(idx, np.full(idx.size, s))
+            want_r = np.where(off < 0, base - 1, base)
+            want_start = want_r * (2 * s - want_r - 1) // 2
+            assert np.array_equal(r, want_r)
+            assert np.array_equal(c, idx - want_start + want_r + 1)
+            assert np.all((r < c) & (c < s))
+
+
+def test_pair_counts_brute_force():
+    from msbm.generator import _pair_counts
+
+    cells = np.array([[3, 1, 0], [2, 2, 4], [1, 0, 5]])
+    clu = np.repeat(np.repeat(np.arange(3), 3), cells.reshape(-1))
+    grp = np.repeat(np.tile(np.arange(3), 3), cells.reshape(-1))
+    n = clu.size
+    want = {(a, b): 0 for a in (True, False) for b in (True, False)}
+    for i in range(n):
+        for j in range(i + 1, n):
+            want[(bool(clu[i] == clu[j]), bool(grp[i] == grp[j]))] += 1
+    assert _pair_counts(cells) == want
+
+
+def test_gaussian_edge_weights_recomputed():
+    """w_ij = exp(-||x_i - x_j||^2 / (2 s^2)) on every stored entry, from the returned features, and
+    symmetric (w_ij = w_ji)."""
+    from msbm.generator import gaussian_edge_weights
+
+    cells = cell_sizes_equal(300, 3, 2)
+    g = sample_msbm(cells, category_probabilities(cells, 12, (0.5, 0.25, 0.15, 0.10)), seed=5)
+    w, r2, x = gaussian_edge_weights(g, dim=4, mean_scale=2.0, bandwidth=1.5, seed=6)
+    rows = np.repeat(np.arange(g.n), np.diff(g.row_ptr))
+    np.testing.assert_allclose(r2, ((x[rows] - x[g.col_idx]) ** 2).sum(axis=1), rtol=1e-12)
+    np.testing.assert_allclose(w, np.exp(-r2 / (2 * 1.5**2)), rtol=1e-12)
+    W = sp.csr_matrix((w, g.col_idx, g.row_ptr), shape=(g.n, g.n))
+    assert abs(W - W.T).max() == 0.0
+    assert np.all((w > 0) & (w <= 1))
