@@ -100,3 +100,27 @@ def test_nonfinite_projected_matrix_is_flagged(eiglib):
     assert eiglib.eig_limited(m, M.ctypes.data, w.ctypes.data, -1) == 0
     M = np.asfortranarray(A.copy())
     assert eiglib.eig_jacobi(m, M.ctypes.data, w.ctypes.data) == 0
+
+
+def test_random_sizes_threaded_and_limited(eiglib):
+    """Sizes across the threaded range (from m = 48 the vectors are formed on several threads while
+    the QR iteration runs), dense, clustered and banded inputs, and calls cut off by a sweep limit."""
+    rng = np.random.default_rng(21)
+    for it in range(40):
+        m = int(rng.integers(40, 257))
+        A = rng.standard_normal((m, m))
+        A = (A + A.T) / 2
+        if it % 3 == 1:  # clustered values, tiny couplings (a converged thick-restart block)
+            A = np.diag(1e-3 * rng.integers(0, 5, m)) + 1e-9 * A
+        elif it % 3 == 2:  # banded (a block-tridiagonal tail)
+            A = np.triu(np.tril(A, 4), -4)
+        M = np.asfortranarray(A.copy())
+        w = np.empty(m)
+        if it % 10 == 9:
+            assert eiglib.eig_limited(m, M.ctypes.data, w.ctypes.data, 2) == 0
+            continue
+        assert eiglib.eig_limited(m, M.ctypes.data, w.ctypes.data, -1) == 1
+        scale = np.abs(A).max()
+        np.testing.assert_allclose(w, np.linalg.eigvalsh(A), atol=1e-12 * scale)
+        np.testing.assert_allclose(M.T @ M, np.eye(m), atol=1e-12)
+        np.testing.assert_allclose(A @ M, M * w, atol=1e-12 * scale)
